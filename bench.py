@@ -1,0 +1,376 @@
+"""Benchmark: one full USPG/USCG reconstruction per step on GB300.
+
+A step is the whole hot path on one batch of synthetic input: coefficient
+generation for the representative views (FP64), per-view simultaneous MART
+(FP32, 5 iterations), and the Cartesian resample -- on the 3D cone-beam
+workload (128 rings x 128 slabs, 90 views over 360 deg, 256x256 detector,
+12 ellipsoids + blob, Poisson noise at 1e5 photons, lambda 0.1).
+
+Metric: MART ray-cell updates per second (nonzeros of the full system matrix
+over all views x iterations, per second of step time).  Also reported:
+ms per MART iteration, the per-phase split, the roofline of the dominant
+kernel (per-launch CUDA-event times), the end-to-end number through the C ABI
+with host buffers, and the FP64 oracle on the host cores (bounded sample).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: one independent reconstruction per rank (replicas; the method has
+no exchange step), value = all ranks' updates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "3d-cone-128r-128s-90v-256"
+METRIC = "MART ray-cell updates/s"
+UNIT = "ray-cell updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+REASON_BITS = {
+    0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+    0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+    0x100: "display_clock_setting",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms",
+                                          "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 4:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, 0
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx = float(s[1])
+                reasons |= int(s[3], 16) if s[3].startswith("0x") else int(s[3])
+            except ValueError:
+                continue
+        names = [n for b, n in REASON_BITS.items() if reasons & b and n != "gpu_idle"]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": names,
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        d = json.load(open(PEAKS_FILE))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------ our path ---
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2208_12964_gb300 import synth, uspg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    spec = synth.workload(args.workload)
+    spec["seed"] = spec["seed"] + 1000 * rank  # each replica reconstructs its own object
+    proj_host = synth.projections(spec)
+    n_views, n_rays = proj_host.shape
+    iters, lam = spec["iterations"], spec["lam"]
+    g, s, o, _ = uspg.descs_from_spec(spec)
+    ctx = uspg.uspg_create(g, s, o)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    proj_dev = torch.from_numpy(proj_host).to(dev)
+    proj_pin = torch.from_numpy(proj_host).pin_memory()
+    R = spec["n_rings"]
+    nx = ny = 2 * R
+    ns = spec["n_slabs"]
+    img_dev = torch.empty((ns, ny, nx), dtype=torch.float32, device=dev)
+    img_pin = torch.empty((ns, ny, nx), dtype=torch.float32).pin_memory()
+    opts, _keep = uspg.mart_opts(iters, lam, uspg.PER_VIEW)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step_device():
+        uspg.uspg_set_projections(ctx, proj_dev, True, sp)
+        uspg.uspg_build_coeffs(ctx, sp)
+        uspg.uspg_fill_image(ctx, 1.0, sp)
+        uspg.uspg_mart(ctx, opts, sp)
+        uspg.uspg_resample_cartesian(ctx, uspg.RESAMPLE_POINT, nx, ny, img_dev, True, sp)
+
+    def step_e2e():
+        uspg.uspg_set_projections(ctx, proj_pin, False, sp)
+        uspg.uspg_build_coeffs(ctx, sp)
+        uspg.uspg_fill_image(ctx, 1.0, sp)
+        uspg.uspg_mart(ctx, opts, sp)
+        uspg.uspg_resample_cartesian(ctx, uspg.RESAMPLE_POINT, nx, ny, img_dev, True, sp)
+        with torch.cuda.stream(stream):
+            img_pin.copy_(img_dev, non_blocking=True)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(fn, k):
+        """per-step device time (CUDA events on the launching stream), L2
+        flushed between steps; returns total ms"""
+        tot = 0.0
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize(dev)
+    st = uspg.uspg_coeff_stats(ctx)
+    updates_per_step = st["nnz_all_views"] * iters
+
+    launches0 = uspg.uspg_kernel_launches()
+    barrier()
+    with ClockSampler(local) as clk:
+        t_dev = timed(step_device, args.steps)
+    barrier()
+    launches = uspg.uspg_kernel_launches() - launches0
+    uspg.uspg_sync(ctx, sp)
+
+    # phase split (separate, after the timed region)
+    def phase_ms(fn, k=2):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_build = phase_ms(lambda: uspg.uspg_build_coeffs(ctx, sp))
+
+    def mart_only():
+        uspg.uspg_fill_image(ctx, 1.0, sp)
+        uspg.uspg_mart(ctx, opts, sp)
+
+    ms_mart = phase_ms(mart_only)
+    ms_resample = phase_ms(lambda: uspg.uspg_resample_cartesian(ctx, uspg.RESAMPLE_POINT, nx, ny, img_dev, True, sp))
+
+    # per-launch kernel times of the dominant phase
+    uspg.uspg_fill_image(ctx, 1.0, sp)
+    fw, bw = uspg.uspg_mart_kernel_times(ctx, opts, iters * n_views, sp)
+
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(2):
+            step_e2e()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t_e2e = timed(step_e2e, args.steps)
+        barrier()
+        e2e = (t_e2e, int(proj_pin.numel() * 4), int(img_pin.numel() * 4))
+
+    t_max = t_dev
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([t_dev, e2e[0] if e2e else 0.0], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt[0])
+        if e2e:
+            e2e = (float(tt[1]), e2e[1], e2e[2])
+    info = dict(stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
+                ms_build=ms_build, ms_mart=ms_mart, ms_resample=ms_resample, fw=fw, bw=bw, e2e=e2e, spec=spec,
+                proj=proj_host)
+    uspg.uspg_destroy(ctx)
+    return info
+
+
+def roofline(info):
+    """Dominant per-view kernel: algorithmic bytes per launch / mean launch time."""
+    st = info["stats"]
+    spec = info["spec"]
+    fw, bw = np.asarray(info["fw"], np.float64), np.asarray(info["bw"], np.float64)
+    n_rays = st["n_rays"]
+    reps = st["n_reps"]
+    nnz_view = st["nnz_all_views"] / st["n_views"]
+    wb = 4
+    # forward: stream the representative rows (index + weight), row pointers,
+    # projections in, per-ray log ratio out; the image (25 MB) is L2-resident
+    fwd_bytes = nnz_view * (4 + wb) + n_rays * (8 + 4 + 4)
+    # backward: stream the cell-major entries (ray id + weight), slice
+    # descriptors, and read+write every image cell once
+    cells = st["n_cells"]
+    bwd_bytes = nnz_view * (4 + wb) + cells * (4 + 4)
+    t_f, t_b = fw.mean(), bw.mean()
+    if t_b >= t_f:
+        name, b, t = "k_backward", bwd_bytes, t_b
+    else:
+        name, b, t = "k_forward", fwd_bytes, t_f
+    peak, src = load_peaks()
+    achieved = b / (t * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": src, "traffic": None,
+            "bytes_per_launch": int(b), "ms_per_launch": round(t, 5),
+            "other": {"k_forward_ms": round(t_f, 5), "k_backward_ms": round(t_b, 5),
+                      "k_forward_GBs": round(fwd_bytes / (t_f * 1e-3) / 1e9, 1),
+                      "k_backward_GBs": round(bwd_bytes / (t_b * 1e-3) / 1e9, 1)}}
+
+
+# ------------------------------------------------------------- oracle ---
+
+def oracle_sample(spec, proj, threads=None, n_views=1):
+    """The FP64 oracle, as it stands, on a bounded sample: per-view MART steps
+    for the first n_views views of the same workload (all rays)."""
+    import oracle
+
+    threads = threads or os.cpu_count() or 1
+    keys = dict(oracle.Problem._fields_)
+    o = oracle.Oracle({k: v for k, v in spec.items() if k in keys}, threads=threads)
+    f = np.ones(o.n_cells)
+    t0 = time.perf_counter()
+    nnz = o.mart_views_sample(proj, f, list(range(n_views)), spec["lam"])
+    dt = time.perf_counter() - t0
+    return nnz / dt, threads, dt, nnz
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2208_12964_gb300 import synth
+
+    spec = synth.workload(args.workload)
+    proj = synth.projections(spec)
+    import oracle
+
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample(spec, proj)
+    vals, tot = [], 0.0
+    for _ in range(args.steps):
+        v, thr, dt, nnz = oracle_sample(spec, proj)
+        vals.append(v)
+        tot += dt
+    val = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": "one per-view MART step (view 0, all 65536 rays)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"one per-view MART step of view 0 ({nnz} ray-cell nonzeros) per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    info = run_ours(args, rank, world, local)
+    if rank != 0:
+        return 0
+    st = info["stats"]
+    K = args.steps
+    ms_step = info["t_ms"] / K
+    value = info["updates_per_step"] * K * world / (info["t_ms"] * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "rings": info["spec"]["n_rings"],
+                       "slabs": info["spec"]["n_slabs"], "views": st["n_views"], "detector": [256, 256],
+                       "iterations": info["spec"]["iterations"], "schedule": "per_view", "coeff_dtype": "f32",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}",
+                       "step": "coefficient build + MART + resample"},
+            "ms_per_iteration": info["ms_mart"] / info["spec"]["iterations"],
+            "phases_ms": {"coefficients": round(info["ms_build"], 3), "mart": round(info["ms_mart"], 3),
+                          "resample": round(info["ms_resample"], 3)},
+            "store": {"reps": st["n_reps"], "nnz_store": st["nnz_store"], "nnz_all_views": st["nnz_all_views"],
+                      "store_bytes": st["store_bytes"], "full_matrix_bytes": st["full_matrix_bytes"]},
+            "gpu_launches": int(info["launches"]),
+            "clocks": info["clk"], "roofline": roofline(info)}
+    if info["e2e"]:
+        t_e2e, hb, db = info["e2e"]
+        line["e2e"] = {"value": info["updates_per_step"] * K * world / (t_e2e * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "ms_per_step": t_e2e / K}
+    if not args.no_cpu_baseline and world == 1:
+        v, thr, dt, nnz = oracle_sample(info["spec"], info["proj"])
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "sample": f"one per-view MART step of view 0 ({nnz} nonzeros, {dt:.1f} s)"}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,227 @@
+/*
+ * libuspg -- GB300 (sm_103a) MART reconstruction on Uniformly Sampled Polar /
+ * Cylindrical Grids, after Chaudhary, Wahi and Munshi, "Uniformly Sampled
+ * Polar and Cylindrical Grid Approach for 2D, 3D Image Reconstruction using
+ * Algebraic Algorithm" (arXiv 2208.12964).
+ *
+ * The calls follow the paper's statement of the problem: a grid (rings,
+ * per-ring sectors, axial slabs), a scan (parallel-beam 2D or cone-beam 3D,
+ * view angles, detector), coefficients of the lines computed once for the
+ * representative views and reused for every other view by rotation, measured
+ * projections in, the field function out (Eq. 17-18), and a Cartesian
+ * resample for display (Sec. II.B).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a uspg_status; no exception crosses this boundary.
+ *    uspg_last_error() gives a message for the last failing call on a
+ *    context (or for a failed uspg_create, through a NULL context).
+ *  - Pointers passed in are borrowed for the duration of the call only; a
+ *    context owns every device and host buffer it allocates.
+ *  - "device" pointers are CUDA global-memory addresses of the current
+ *    device (for example a torch tensor's data_ptr()); "host" pointers are
+ *    ordinary process memory.
+ *  - A uspg_stream is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Device work is enqueued on it and the call returns
+ *    without waiting unless it says otherwise; faults raised inside a kernel
+ *    (a bounds flag, a wait that gave up) are reported by uspg_sync().
+ *  - Layouts: cells of a slab are numbered ring by ring from the axis
+ *    outward, each ring counter-clockwise from the +x axis starting at its
+ *    head H_n (Eq. 2); cell id = slab * cells_per_slab + H_ring + sector.
+ *    Images are float32 [slabs][cells_per_slab].  Projections are float32
+ *    [views][rays]; 2D ray = detector bin, 3D ray = v_row * n_u + u_col.
+ *  - Not thread-safe per context: one host thread (or external locking) per
+ *    uspg_ctx.  Distinct contexts are independent.
+ */
+#ifndef USPG_H
+#define USPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    USPG_OK = 0,
+    USPG_EINVAL = 1,       /* bad argument or geometry */
+    USPG_ENOMEM = 2,       /* device or host allocation failed */
+    USPG_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    USPG_ETIMEOUT = 4,     /* a device-side wait gave up (reported by uspg_sync) */
+    USPG_EUNSUPPORTED = 5, /* valid request this build does not serve */
+    USPG_EBUSY = 6,        /* server: no slot or memory for the job now */
+    USPG_ENOTREADY = 7,    /* coefficients not built / result not finished */
+    USPG_EDEVICE = 8       /* a kernel raised its bounds/consistency flag */
+} uspg_status;
+
+/* sector rules (Sec. II.A) */
+enum { USPG_SECT_6N = 0, USPG_SECT_4_2N1 = 1, USPG_SECT_CUSTOM = 2 };
+/* scan geometries (Sec. III, Table 1) */
+enum { USPG_PARALLEL_2D = 0, USPG_CONE_3D = 1 };
+/* coefficient models (Sec. III.B) */
+enum { USPG_LENGTH = 0, USPG_BINARY = 1 };
+/* stored coefficient precision */
+enum { USPG_F32 = 0, USPG_F16 = 1, USPG_BF16 = 2 };
+/* MART schedules (Sec. III.D) */
+enum { USPG_SEQUENTIAL = 0, USPG_PER_VIEW = 1 };
+/* update rules: POWER f *= (P/Pbar)^(lambda w/max w); LINEAR_EQ18 f *= 1 - lambda (1 - P/Pbar) */
+enum { USPG_POWER = 0, USPG_LINEAR_EQ18 = 1 };
+/* resample modes (Sec. II.B) */
+enum { USPG_RESAMPLE_POINT = 0, USPG_RESAMPLE_BIJECTION = 1 };
+
+typedef void *uspg_stream;
+typedef struct uspg_ctx uspg_ctx;
+
+/* Grid (Sec. II.A-B, Sec. III.C).  Ring n (1-based) spans radii
+ * [(n-1) r, n r]; it has 6n sectors (SECT_6N), 4(2n-1) sectors (SECT_4_2N1,
+ * Eq. 1) or sectors[n-1] (SECT_CUSTOM).  n_slabs = 1 with a parallel scan is
+ * the 2D grid; a cone scan stacks n_slabs slabs of height slab_height from
+ * z_min.  Limits: n_rings <= 1024, n_slabs <= 1024, sectors per ring <= 4096,
+ * total cells < 2^31. */
+typedef struct {
+    int32_t n_rings;
+    int32_t sector_rule;
+    const int32_t *sectors; /* host, [n_rings], used only for SECT_CUSTOM */
+    double ring_width;      /* r; the grid radius is n_rings * r */
+    int32_t n_slabs;
+    int32_t reserved;
+    double slab_height;
+    double z_min;
+} uspg_grid_desc;
+
+/* Scan (Sec. III.C, Table 1).  View k (0-based) is at k * arc / n_views turns,
+ * arc = arc_num/arc_den turns (1/2 for a parallel half-turn, 1 for a cone full
+ * turn).  Parallel 2D: n_u bins of width du centred on the axis, n_v = 1; the
+ * rays of view 0 run along +y.  Cone 3D: source at (-src_to_axis, 0, 0), flat
+ * detector of n_u x n_v pixels (pitch du, dv) centred at
+ * (src_to_det - src_to_axis, 0, 0) with u along +y and v along +z; the set
+ * rotates about z. */
+typedef struct {
+    int32_t geometry;
+    int32_t n_views;
+    int64_t arc_num, arc_den;
+    int32_t n_u, n_v;
+    double du, dv;
+    double src_to_axis, src_to_det;
+} uspg_scan_desc;
+
+typedef struct {
+    int32_t weight_mode; /* USPG_LENGTH | USPG_BINARY */
+    int32_t coeff_dtype; /* USPG_F32 | USPG_F16 | USPG_BF16 */
+    int32_t reserved0, reserved1;
+} uspg_coeff_opts;
+
+typedef struct {
+    int32_t iterations;
+    int32_t schedule;    /* USPG_SEQUENTIAL | USPG_PER_VIEW */
+    int32_t update_rule; /* USPG_POWER | USPG_LINEAR_EQ18 (sequential only) */
+    int32_t reserved;
+    double lambda;             /* relaxation (beta of Eq. 18), in (0, 2) */
+    double stop_tol;           /* Eq. 19 tolerance; 0 = run all iterations */
+    const int32_t *view_order; /* host, [n_views] permutation for PER_VIEW; NULL = 0..n_views-1 */
+} uspg_mart_opts;
+
+typedef struct {
+    int64_t n_cells, cells_per_slab, n_rays, n_views, n_reps;
+    int64_t nnz_store;         /* nonzeros held for the representative views */
+    int64_t nnz_all_views;     /* nonzeros of the full matrix over all views */
+    int64_t store_bytes;       /* device bytes of the coefficient store (both layouts) */
+    int64_t full_matrix_bytes; /* bytes the same layouts would need for every view */
+    int64_t max_row;           /* longest row (entries) */
+    int64_t gcd;               /* rotational symmetry order G of the grid */
+} uspg_stats;
+
+/* --- context -------------------------------------------------------------- */
+
+/* Validates the description, builds the grid tables (Eq. 1-2) and the view
+ * classes (views that share stored rows, Sec. III.C), and allocates nothing
+ * on the device yet.  *out receives a new context or NULL.  EINVAL on a
+ * non-positive size, sectors < 1, limits exceeded, or a cone detector that
+ * misses the cylinder. */
+uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, const uspg_coeff_opts *opts,
+                        uspg_ctx **out);
+/* Frees the context and all its device memory (waits for its work first). */
+void uspg_destroy(uspg_ctx *ctx);
+/* Message for the last failing call on ctx (ctx may be NULL: last failed create). */
+const char *uspg_last_error(const uspg_ctx *ctx);
+/* Waits for the context's work on `stream` and reports device-side flags:
+ * EDEVICE (bounds / store overflow) or ETIMEOUT (a bounded wait gave up). */
+uspg_status uspg_sync(uspg_ctx *ctx, uspg_stream stream);
+
+/* --- coefficients (Sec. III.A-C, Algorithm 1) -------------------------------- */
+
+/* Traces every ray of every representative view in FP64 (cylinder roots of
+ * Eq. 3-4 formed as (mr-d)(mr+d), axial and radial plane crossings, midpoint
+ * cell assignment of Eq. 5-10, pieces < 1e-9 of a cell dropped, repeated cells
+ * merged) and stores the rows twice: ray-major for the forward ray sums and
+ * cell-major for the correction.  Replaces any earlier store. */
+uspg_status uspg_build_coeffs(uspg_ctx *ctx, uspg_stream stream);
+uspg_status uspg_coeff_stats(const uspg_ctx *ctx, uspg_stats *out);
+/* Host copy of row `ray` of view `view` as the MART kernels see it (stored
+ * representative row, sectors rotated to the view).  cells: host int64[cap],
+ * w: host double[cap] (the stored precision widened), *n = entries; if the
+ * row is longer than cap, *n = its length and nothing is copied (EINVAL).
+ * Synchronous. */
+uspg_status uspg_get_row(const uspg_ctx *ctx, int32_t view, int32_t ray, int32_t cap, int64_t *cells, double *w,
+                         int32_t *n);
+
+/* --- data in / out ------------------------------------------------------------ */
+
+/* Projections P_{p,l} of Eq. 17, float32 [views][rays], copied into the
+ * context (host source: staged with cudaMemcpyAsync, so the call may return
+ * before the copy ends only for page-locked memory). */
+uspg_status uspg_set_projections(uspg_ctx *ctx, const float *p, int32_t on_device, uspg_stream stream);
+/* Image f_v, float32 [cells]. */
+uspg_status uspg_set_image(uspg_ctx *ctx, const float *f, int32_t on_device, uspg_stream stream);
+/* Sets every cell of the image to `value` (the paper starts from an arbitrary
+ * field; the workloads start from 1). */
+uspg_status uspg_fill_image(uspg_ctx *ctx, float value, uspg_stream stream);
+uspg_status uspg_get_image(const uspg_ctx *ctx, float *f, int32_t to_device, uspg_stream stream);
+
+/* --- reconstruction (Sec. III.D, Eq. 17-19) ---------------------------------- */
+
+/* Runs MART on the context's image with its projections.
+ * SEQUENTIAL: views 0..p-1 in order, rays in order, each ray's cells corrected
+ *   before the next ray (one persistent kernel).
+ * PER_VIEW: for each view of view_order, all ray sums with the current image,
+ *   then each cell corrected once by the weighted geometric mean of its rays'
+ *   ratios (P = 0 rays zero their cells).
+ * With stop_tol > 0 (SEQUENTIAL), stops after the first sweep in which every
+ * correction satisfies Eq. 19.  ENOTREADY without coefficients or projections. */
+uspg_status uspg_mart(uspg_ctx *ctx, const uspg_mart_opts *opts, uspg_stream stream);
+/* Forward projection of one view with the current image (Eq. 17):
+ * out = device float32 [rays]. */
+uspg_status uspg_forward_project(uspg_ctx *ctx, int32_t view, float *out, uspg_stream stream);
+/* Sweeps run by the last uspg_mart (SEQUENTIAL with stop_tol > 0: may be
+ * fewer than requested).  Synchronous. */
+uspg_status uspg_mart_sweeps(uspg_ctx *ctx, int32_t *sweeps);
+
+/* --- display (Sec. II.B) ------------------------------------------------------- */
+
+/* USPG -> Cartesian.  POINT: an nx x ny image over [-R, R]^2 per slab, each
+ * pixel the cell holding its centre (0 outside the disk).  BIJECTION (grids
+ * with 4(2n-1) sectors only, nx = ny = 2 n_rings): square ring n of the image
+ * takes the cells of ring n in the same counter-clockwise order from +x.
+ * out: float32 [slabs][ny][nx], device (out_on_device = 1) or host. */
+uspg_status uspg_resample_cartesian(uspg_ctx *ctx, int32_t mode, int32_t nx, int32_t ny, float *out,
+                                    int32_t out_on_device, uspg_stream stream);
+
+/* --- instrumentation ------------------------------------------------------------ */
+
+/* Kernels launched by this library in this process (graph replays count each
+ * kernel node). */
+int64_t uspg_kernel_launches(void);
+/* Runs PER_VIEW MART exactly as uspg_mart does, but launches its kernels one
+ * by one with a CUDA event between consecutive launches on `stream`, and
+ * returns each launch's device time: ms_forward[i], ms_backward[i] for the
+ * i-th view step (host float arrays of length cap >= iterations * n_views;
+ * *n = steps written).  Synchronous.  For measurement only: the result
+ * image equals uspg_mart's. */
+uspg_status uspg_mart_kernel_times(uspg_ctx *ctx, const uspg_mart_opts *opts, float *ms_forward, float *ms_backward,
+                                   int32_t cap, int32_t *n, uspg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* USPG_H */

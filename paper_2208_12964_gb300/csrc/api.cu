@@ -1,0 +1,582 @@
+// C-ABI host runtime of libuspg (include/uspg.h): context set-up, grid tables
+// (Eq. 1-2), view classes (Sec. III.C), device buffers, data movement, the
+// MART driver and its CUDA-graph cache.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <sstream>
+
+namespace uspg {
+
+static thread_local std::string g_create_err;
+
+uspg_status fail(uspg_ctx *c, uspg_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+uspg_status cuda_fail(uspg_ctx *c, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? USPG_ENOMEM : USPG_ECUDA, m);
+}
+
+static long long gcd_ll(long long a, long long b)
+{
+    while (b) {
+        long long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a < 0 ? -a : a;
+}
+
+static void free_store(uspg_ctx *c)
+{
+    cudaFree(c->d_row_ptr);
+    cudaFree(c->d_idx);
+    cudaFree(c->d_w);
+    cudaFree(c->d_rowmax);
+    cudaFree(c->d_slice_off);
+    cudaFree(c->d_slice_meta);
+    cudaFree(c->d_slice_width);
+    cudaFree(c->d_sray);
+    cudaFree(c->d_sw);
+    cudaFree(c->d_counts);
+    cudaFree(c->d_rep_view);
+    cudaFree(c->d_cell_cnt);
+    cudaFree(c->d_cell_fill);
+    cudaFree(c->d_rel);
+    cudaFree(c->d_w64);
+    c->d_counts = c->d_rep_view = c->d_cell_cnt = c->d_cell_fill = nullptr;
+    c->d_rel = nullptr;
+    c->d_w64 = nullptr;
+    c->cap_idx = c->cap_w = c->cap_w64 = c->cap_sell = 0;
+    c->d_row_ptr = nullptr;
+    c->d_idx = nullptr;
+    c->d_w = nullptr;
+    c->d_rowmax = nullptr;
+    c->d_slice_off = nullptr;
+    c->d_slice_meta = nullptr;
+    c->d_slice_width = nullptr;
+    c->d_sray = nullptr;
+    c->d_sw = nullptr;
+    c->built = false;
+    for (auto &kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    c->graphs.clear();
+}
+
+// device buffers that do not depend on the store
+static uspg_status ensure_state(uspg_ctx *c)
+{
+    if (c->d_ring) return USPG_OK;
+    std::vector<RingEntry> rt(c->n_rings);
+    int chunk = 0;
+    for (int i = 0; i < c->n_rings; i++) {
+        rt[i].head = c->head[i];
+        rt[i].ng = c->ng[i];
+        rt[i].step = c->ng[i] / c->G;
+        rt[i].chunk0 = chunk;
+        chunk += (c->ng[i] + kSlice - 1) / kSlice;
+    }
+    c->slices_per_slab = chunk;
+    c->slices_per_rep = (long long)chunk * (c->scan.geometry == USPG_CONE_3D ? c->n_slabs : 1);
+    USPG_CUDA(c, cudaMalloc(&c->d_ring, sizeof(RingEntry) * c->n_rings));
+    USPG_CUDA(c, cudaMemcpy(c->d_ring, rt.data(), sizeof(RingEntry) * c->n_rings, cudaMemcpyHostToDevice));
+    USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * c->n_cells));
+    USPG_CUDA(c, cudaMalloc(&c->d_proj, sizeof(float) * (long long)c->scan.n_views * c->n_rays));
+    USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * c->n_rays));
+    USPG_CUDA(c, cudaMalloc(&c->d_status, sizeof(int)));
+    USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    USPG_CUDA(c, cudaMalloc(&c->d_sweeps, sizeof(int)));
+    USPG_CUDA(c, cudaMemset(c->d_sweeps, 0, sizeof(int)));
+    USPG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    return USPG_OK;
+}
+
+}  // namespace uspg
+
+using namespace uspg;
+
+extern "C" {
+
+int64_t uspg_kernel_launches(void) { return launch_counter(); }
+
+const char *uspg_last_error(const uspg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, const uspg_coeff_opts *opts,
+                        uspg_ctx **out)
+{
+    if (!out) return fail(nullptr, USPG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !scan) return fail(nullptr, USPG_EINVAL, "grid and scan descriptions are required");
+    const uspg_grid_desc &g = *grid;
+    const uspg_scan_desc &s = *scan;
+    if (g.n_rings < 1 || g.n_rings > kMaxRings) return fail(nullptr, USPG_EINVAL, "n_rings must be in [1, 1024]");
+    if (!(g.ring_width > 0.0) || !std::isfinite(g.ring_width)) return fail(nullptr, USPG_EINVAL, "ring_width must be > 0");
+    if (s.geometry != USPG_PARALLEL_2D && s.geometry != USPG_CONE_3D)
+        return fail(nullptr, USPG_EINVAL, "unknown scan geometry");
+    int ns = s.geometry == USPG_CONE_3D ? g.n_slabs : 1;
+    if (s.geometry == USPG_PARALLEL_2D && g.n_slabs != 1)
+        return fail(nullptr, USPG_EINVAL, "a parallel 2D scan needs n_slabs = 1");
+    if (ns < 1 || ns > kMaxSlabs) return fail(nullptr, USPG_EINVAL, "n_slabs must be in [1, 1024]");
+    if (s.geometry == USPG_CONE_3D && !(g.slab_height > 0.0)) return fail(nullptr, USPG_EINVAL, "slab_height must be > 0");
+    if (s.n_views < 1 || s.n_u < 1 || s.n_v < 1 || s.arc_den < 1 || s.arc_num < 0)
+        return fail(nullptr, USPG_EINVAL, "n_views, n_u, n_v, arc_den must be >= 1 and arc_num >= 0");
+    if (s.geometry == USPG_PARALLEL_2D && s.n_v != 1) return fail(nullptr, USPG_EINVAL, "parallel 2D scans have n_v = 1");
+    if (!(s.du > 0.0) || (s.geometry == USPG_CONE_3D && !(s.dv > 0.0)))
+        return fail(nullptr, USPG_EINVAL, "detector pitch must be > 0");
+    if ((long long)s.n_u * s.n_v >= (1LL << 31)) return fail(nullptr, USPG_EINVAL, "too many rays per view");
+    double R = g.n_rings * g.ring_width;
+    if (s.geometry == USPG_CONE_3D) {
+        if (!(s.src_to_axis > R) || !(s.src_to_det > s.src_to_axis))
+            return fail(nullptr, USPG_EINVAL, "cone scan needs src_to_det > src_to_axis > grid radius");
+        // the detector must see the cylinder: its half-width at the axis must exceed 0
+        double half_u = 0.5 * s.n_u * s.du * s.src_to_axis / s.src_to_det;
+        if (!(half_u > 0.0)) return fail(nullptr, USPG_EINVAL, "detector misses the object");
+    } else {
+        double half = 0.5 * s.n_u * s.du;
+        if (!(half > 0.0)) return fail(nullptr, USPG_EINVAL, "detector misses the object");
+    }
+    int wm = opts ? opts->weight_mode : USPG_LENGTH;
+    int dt = opts ? opts->coeff_dtype : USPG_F32;
+    if (wm != USPG_LENGTH && wm != USPG_BINARY) return fail(nullptr, USPG_EINVAL, "unknown weight_mode");
+    if (dt != USPG_F32 && dt != USPG_F16 && dt != USPG_BF16) return fail(nullptr, USPG_EINVAL, "unknown coeff_dtype");
+
+    uspg_ctx *c = new uspg_ctx();
+    c->n_rings = g.n_rings;
+    c->sector_rule = g.sector_rule;
+    c->n_slabs = ns;
+    c->r = g.ring_width;
+    c->h = s.geometry == USPG_CONE_3D ? g.slab_height : 1.0;
+    c->z_min = s.geometry == USPG_CONE_3D ? g.z_min : 0.0;
+    c->scan = s;
+    c->n_rays = s.n_u * (s.geometry == USPG_CONE_3D ? s.n_v : 1);
+    c->weight_mode = wm;
+    c->dtype = dt;
+    double unit = c->r;
+    if (s.geometry == USPG_CONE_3D && c->h < unit) unit = c->h;
+    c->w_scale = dt == USPG_F32 ? 1.0 : unit;
+    // Eq. 1 and Eq. 2: sector counts and heads
+    c->ng.resize(g.n_rings);
+    c->head.resize(g.n_rings);
+    long long hsum = 0, G = 0;
+    for (int n = 1; n <= g.n_rings; n++) {
+        long long k;
+        if (g.sector_rule == USPG_SECT_6N) k = 6LL * n;
+        else if (g.sector_rule == USPG_SECT_4_2N1) k = 4LL * (2 * n - 1);
+        else if (g.sector_rule == USPG_SECT_CUSTOM) {
+            if (!g.sectors) {
+                delete c;
+                return fail(nullptr, USPG_EINVAL, "SECT_CUSTOM needs a sectors table");
+            }
+            k = g.sectors[n - 1];
+        } else {
+            delete c;
+            return fail(nullptr, USPG_EINVAL, "unknown sector rule");
+        }
+        if (k < 1 || k > kMaxSectors) {
+            delete c;
+            return fail(nullptr, USPG_EINVAL, "sectors per ring must be in [1, 4096]");
+        }
+        c->ng[n - 1] = (int)k;
+        c->head[n - 1] = (int)hsum;
+        hsum += k;
+        G = gcd_ll(G, k);
+    }
+    if (c->ng[0] > 2 * kMaxRing0Cross - 4) {
+        delete c;
+        return fail(nullptr, USPG_EUNSUPPORTED, "the innermost ring may have at most 60 sectors");
+    }
+    c->cells_per_slab = hsum;
+    c->n_cells = hsum * ns;
+    c->G = (int)G;
+    if (c->n_cells >= (1LL << 31)) {
+        delete c;
+        return fail(nullptr, USPG_EINVAL, "grid has 2^31 cells or more");
+    }
+    // Sec. III.C: view k at theta_k = k*arc/p turns = m_k/G + rho_k; views with
+    // equal residual rho_k share the stored rows of the first of them.
+    int nv = s.n_views;
+    long long den = s.arc_den * (long long)nv;
+    c->rep_of_view.assign(nv, -1);
+    c->m_of_view.assign(nv, 0);
+    std::map<long long, int> first_of_key;
+    for (int k = 0; k < nv; k++) {
+        long long num = (long long)k * s.arc_num * G;
+        long long m = num / den, key = num % den;
+        auto it = first_of_key.find(key);
+        if (it == first_of_key.end()) {
+            first_of_key[key] = (int)c->rep_view.size();
+            c->rep_of_view[k] = (int)c->rep_view.size();
+            c->rep_view.push_back(k);
+            c->m_of_view[k] = 0;
+        } else {
+            int rep = it->second;
+            long long mrep = ((long long)c->rep_view[rep] * s.arc_num * G) / den;
+            c->rep_of_view[k] = rep;
+            c->m_of_view[k] = (int)(m - mrep);
+        }
+    }
+    c->n_reps = (int)c->rep_view.size();
+    *out = c;
+    return USPG_OK;
+}
+
+void uspg_destroy(uspg_ctx *c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_store(c);
+    cudaFree(c->d_ring);
+    cudaFree(c->d_bdir);
+    cudaFree(c->d_f);
+    cudaFree(c->d_proj);
+    cudaFree(c->d_res);
+    cudaFree(c->d_status);
+    cudaFree(c->d_sweeps);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+uspg_status uspg_sync(uspg_ctx *c, uspg_stream stream)
+{
+    if (!c) return fail(nullptr, USPG_EINVAL, "NULL context");
+    USPG_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+    if (!c->d_status) return USPG_OK;
+    int st = 0;
+    USPG_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+        if (st & kStatusTimeout) return fail(c, USPG_ETIMEOUT, "a device-side wait gave up");
+        std::ostringstream os;
+        os << "device flag 0x" << std::hex << st << ": ";
+        if (st & kStatusCountMismatch) os << "row count changed between generator passes; ";
+        if (st & kStatusRing0Overflow) os << "too many crossings in the innermost ring; ";
+        if (st & kStatusBounds) os << "index out of range; ";
+        return fail(c, USPG_EDEVICE, os.str());
+    }
+    return USPG_OK;
+}
+
+uspg_status uspg_build_coeffs(uspg_ctx *c, uspg_stream stream)
+{
+    if (!c) return fail(nullptr, USPG_EINVAL, "NULL context");
+    uspg_status st = ensure_state(c);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    c->built = false;
+    c->store_moved = false;
+    st = build_store(c, s);
+    if (st) return st;
+    if (c->store_moved) {  // captured graphs point at the old buffers
+        for (auto &kv : c->graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        c->graphs.clear();
+    }
+    st = uspg_sync(c, stream);
+    if (st) return st;
+    c->built = true;
+    return USPG_OK;
+}
+
+uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
+{
+    if (!c || !o) return fail(const_cast<uspg_ctx *>(c), USPG_EINVAL, "NULL argument");
+    if (!c->built) return fail(const_cast<uspg_ctx *>(c), USPG_ENOTREADY, "coefficients not built");
+    int wb = c->dtype == USPG_F32 ? 4 : 2;
+    o->n_cells = c->n_cells;
+    o->cells_per_slab = c->cells_per_slab;
+    o->n_rays = c->n_rays;
+    o->n_views = c->scan.n_views;
+    o->n_reps = c->n_reps;
+    o->nnz_store = c->gen.nnz;
+    o->nnz_all_views = c->nnz_all_views;
+    long long rows = (long long)c->n_reps * c->n_rays;
+    long long slices = c->slices_per_rep * c->n_reps;
+    o->store_bytes = c->gen.nnz_pad * (4 + wb) + (rows + 1) * 8 + rows * 4 + c->gen.sell_entries * (4 + wb) +
+                     slices * (8 + 4 + 4);
+    double per_view = c->n_reps ? (double)o->store_bytes / c->n_reps : 0.0;
+    o->full_matrix_bytes = (int64_t)(per_view * c->scan.n_views);
+    o->max_row = c->gen.max_row;
+    o->gcd = c->G;
+    return USPG_OK;
+}
+
+uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t cap, int64_t *cells, double *w,
+                         int32_t *n)
+{
+    uspg_ctx *c = const_cast<uspg_ctx *>(cc);
+    if (!c || !n) return fail(c, USPG_EINVAL, "NULL argument");
+    if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    if (view < 0 || view >= c->scan.n_views || ray < 0 || ray >= c->n_rays) return fail(c, USPG_EINVAL, "bad view/ray");
+    int rep = c->rep_of_view[view];
+    long long row = (long long)rep * c->n_rays + ray;
+    long long b = c->h_row_ptr[row], e = c->h_row_ptr[row + 1];
+    std::vector<uint32_t> ix(e - b);
+    int wb = c->dtype == USPG_F32 ? 4 : 2;
+    std::vector<unsigned char> wr((e - b) * wb);
+    if (e > b) {
+        USPG_CUDA(c, cudaMemcpy(ix.data(), c->d_idx + b, sizeof(uint32_t) * (e - b), cudaMemcpyDeviceToHost));
+        USPG_CUDA(c, cudaMemcpy(wr.data(), (char *)c->d_w + b * wb, wb * (e - b), cudaMemcpyDeviceToHost));
+    }
+    int mG = c->m_of_view[view] % c->G;
+    int cnt = 0;
+    for (long long q = 0; q < e - b; q++) {
+        double wv;
+        if (c->dtype == USPG_F32) {
+            float f;
+            std::memcpy(&f, &wr[q * 4], 4);
+            wv = f;
+        } else {
+            uint16_t u;
+            std::memcpy(&u, &wr[q * 2], 2);
+            if (c->dtype == USPG_BF16) {
+                uint32_t x = (uint32_t)u << 16;
+                float f;
+                std::memcpy(&f, &x, 4);
+                wv = f;
+            } else {
+                __half_raw hr;
+                hr.x = u;
+                wv = (double)__half2float(__half(hr));
+            }
+        }
+        if (!(wv > 0.0)) continue;  // row padding
+        if (cnt < cap && cells && w) {
+            uint32_t pc = ix[q];
+            int ring = cell_ring(pc), ng = c->ng[ring];
+            int sec = (cell_sector(pc) + mG * (ng / c->G)) % ng;
+            cells[cnt] = (long long)cell_slab(pc) * c->cells_per_slab + c->head[ring] + sec;
+            w[cnt] = wv * c->w_scale;
+        }
+        cnt++;
+    }
+    *n = cnt;
+    if (cnt > cap) return fail(c, USPG_EINVAL, "row longer than cap");
+    return USPG_OK;
+}
+
+uspg_status uspg_set_projections(uspg_ctx *c, const float *p, int32_t on_device, uspg_stream stream)
+{
+    if (!c || !p) return fail(c, USPG_EINVAL, "NULL argument");
+    uspg_status st = ensure_state(c);
+    if (st) return st;
+    size_t bytes = sizeof(float) * (size_t)c->scan.n_views * c->n_rays;
+    USPG_CUDA(c, cudaMemcpyAsync(c->d_proj, p, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 (cudaStream_t)stream));
+    c->have_proj = true;
+    return USPG_OK;
+}
+
+uspg_status uspg_set_image(uspg_ctx *c, const float *f, int32_t on_device, uspg_stream stream)
+{
+    if (!c || !f) return fail(c, USPG_EINVAL, "NULL argument");
+    uspg_status st = ensure_state(c);
+    if (st) return st;
+    USPG_CUDA(c, cudaMemcpyAsync(c->d_f, f, sizeof(float) * c->n_cells,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    return USPG_OK;
+}
+
+__global__ void k_fill_value(float *f, long long n, float v)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = v;
+}
+
+uspg_status uspg_fill_image(uspg_ctx *c, float value, uspg_stream stream)
+{
+    if (!c) return fail(c, USPG_EINVAL, "NULL context");
+    uspg_status st = ensure_state(c);
+    if (st) return st;
+    k_fill_value<<<(unsigned)((c->n_cells + 255) / 256), 256, 0, (cudaStream_t)stream>>>(c->d_f, c->n_cells, value);
+    launch_counter()++;
+    USPG_CUDA(c, cudaGetLastError());
+    return USPG_OK;
+}
+
+uspg_status uspg_get_image(const uspg_ctx *cc, float *f, int32_t to_device, uspg_stream stream)
+{
+    uspg_ctx *c = const_cast<uspg_ctx *>(cc);
+    if (!c || !f) return fail(c, USPG_EINVAL, "NULL argument");
+    if (!c->d_f) return fail(c, USPG_ENOTREADY, "no image");
+    USPG_CUDA(c, cudaMemcpyAsync(f, c->d_f, sizeof(float) * c->n_cells,
+                                 to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    return USPG_OK;
+}
+
+// per-view simultaneous MART as one CUDA graph per option set
+static uspg_status per_view(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s)
+{
+    int nv = c->scan.n_views;
+    std::vector<int> order(nv);
+    if (o->view_order) {
+        std::vector<char> seen(nv, 0);
+        for (int q = 0; q < nv; q++) {
+            int k = o->view_order[q];
+            if (k < 0 || k >= nv || seen[k]) return fail(c, USPG_EINVAL, "view_order is not a permutation");
+            seen[k] = 1;
+            order[q] = k;
+        }
+    } else {
+        std::iota(order.begin(), order.end(), 0);
+    }
+    std::ostringstream key;
+    key << o->iterations << ':' << o->lambda;
+    for (int k : order) key << ',' << k;
+    auto it = c->graphs.find(key.str());
+    if (it == c->graphs.end()) {
+        Graph g;
+        cudaStream_t cs = c->cap_stream;
+        int64_t before = launch_counter();
+        USPG_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        uspg_status st = USPG_OK;
+        for (int itn = 0; itn < o->iterations && !st; itn++)
+            for (int q = 0; q < nv && !st; q++) {
+                st = launch_forward_view(c, order[q], nullptr, c->d_res, cs);
+                if (!st) st = launch_backward_view(c, order[q], (float)o->lambda, cs);
+            }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        USPG_CUDA(c, e);
+        g.graph = graph;
+        g.nodes = launch_counter() - before;
+        launch_counter() = before;  // captured, not launched
+        USPG_CUDA(c, cudaGraphInstantiate(&g.exec, graph, 0));
+        it = c->graphs.emplace(key.str(), g).first;
+    }
+    USPG_CUDA(c, cudaGraphLaunch(it->second.exec, s));
+    launch_counter() += it->second.nodes;
+    return USPG_OK;
+}
+
+uspg_status uspg_mart(uspg_ctx *c, const uspg_mart_opts *o, uspg_stream stream)
+{
+    if (!c || !o) return fail(c, USPG_EINVAL, "NULL argument");
+    if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    if (!c->have_proj) return fail(c, USPG_ENOTREADY, "projections not set");
+    if (o->iterations < 0) return fail(c, USPG_EINVAL, "iterations must be >= 0");
+    if (!(o->lambda > 0.0) || !(o->lambda < 2.0)) return fail(c, USPG_EINVAL, "lambda must be in (0, 2)");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_sweeps = o->iterations;
+    if (o->iterations == 0) return USPG_OK;
+    if (o->schedule == USPG_SEQUENTIAL) {
+        if (o->update_rule != USPG_POWER && o->update_rule != USPG_LINEAR_EQ18)
+            return fail(c, USPG_EINVAL, "unknown update rule");
+        if (o->stop_tol < 0.0) return fail(c, USPG_EINVAL, "stop_tol must be >= 0");
+        c->last_sweeps = -1;
+        return launch_sequential(c, o, s);
+    }
+    if (o->schedule != USPG_PER_VIEW) return fail(c, USPG_EINVAL, "unknown schedule");
+    if (o->update_rule != USPG_POWER)
+        return fail(c, USPG_EUNSUPPORTED, "the per-view schedule uses the power (geometric-mean) update");
+    if (o->stop_tol != 0.0) return fail(c, USPG_EUNSUPPORTED, "stop_tol applies to the sequential schedule");
+    return per_view(c, o, s);
+}
+
+uspg_status uspg_mart_kernel_times(uspg_ctx *c, const uspg_mart_opts *o, float *ms_fwd, float *ms_bwd, int32_t cap,
+                                   int32_t *n, uspg_stream stream)
+{
+    if (!c || !o || !ms_fwd || !ms_bwd || !n) return fail(c, USPG_EINVAL, "NULL argument");
+    if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    if (!c->have_proj) return fail(c, USPG_ENOTREADY, "projections not set");
+    if (o->schedule != USPG_PER_VIEW) return fail(c, USPG_EINVAL, "kernel timing covers the per-view schedule");
+    int nv = c->scan.n_views;
+    long long steps = (long long)o->iterations * nv;
+    if (steps > cap) return fail(c, USPG_EINVAL, "cap < iterations * n_views");
+    std::vector<int> order(nv);
+    for (int q = 0; q < nv; q++) order[q] = o->view_order ? o->view_order[q] : q;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<cudaEvent_t> ev(2 * steps + 1);
+    for (auto &e : ev) USPG_CUDA(c, cudaEventCreate(&e));
+    USPG_CUDA(c, cudaEventRecord(ev[0], s));
+    long long q = 0;
+    uspg_status st = USPG_OK;
+    for (int it = 0; it < o->iterations && !st; it++)
+        for (int v = 0; v < nv && !st; v++, q++) {
+            st = launch_forward_view(c, order[v], nullptr, c->d_res, s);
+            if (!st) st = (uspg_status)(cudaEventRecord(ev[2 * q + 1], s) ? USPG_ECUDA : USPG_OK);
+            if (!st) st = launch_backward_view(c, order[v], (float)o->lambda, s);
+            if (!st) st = (uspg_status)(cudaEventRecord(ev[2 * q + 2], s) ? USPG_ECUDA : USPG_OK);
+        }
+    cudaError_t e = cudaStreamSynchronize(s);
+    for (long long i = 0; i < steps && !st && e == cudaSuccess; i++) {
+        cudaEventElapsedTime(&ms_fwd[i], ev[2 * i], ev[2 * i + 1]);
+        cudaEventElapsedTime(&ms_bwd[i], ev[2 * i + 1], ev[2 * i + 2]);
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (st) return st;
+    USPG_CUDA(c, e);
+    *n = (int32_t)steps;
+    return USPG_OK;
+}
+
+uspg_status uspg_mart_sweeps(uspg_ctx *c, int32_t *sweeps)
+{
+    if (!c || !sweeps) return fail(c, USPG_EINVAL, "NULL argument");
+    if (c->last_sweeps >= 0) {
+        *sweeps = c->last_sweeps;
+        return USPG_OK;
+    }
+    int v = 0;
+    USPG_CUDA(c, cudaMemcpy(&v, c->d_sweeps, sizeof(int), cudaMemcpyDeviceToHost));
+    *sweeps = v;
+    return USPG_OK;
+}
+
+uspg_status uspg_forward_project(uspg_ctx *c, int32_t view, float *out, uspg_stream stream)
+{
+    if (!c || !out) return fail(c, USPG_EINVAL, "NULL argument");
+    if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    if (view < 0 || view >= c->scan.n_views) return fail(c, USPG_EINVAL, "bad view");
+    return launch_forward_view(c, view, out, nullptr, (cudaStream_t)stream);
+}
+
+uspg_status uspg_resample_cartesian(uspg_ctx *c, int32_t mode, int32_t nx, int32_t ny, float *out,
+                                    int32_t out_on_device, uspg_stream stream)
+{
+    if (!c || !out) return fail(c, USPG_EINVAL, "NULL argument");
+    uspg_status st = ensure_state(c);
+    if (st) return st;
+    int ns = c->scan.geometry == USPG_CONE_3D ? c->n_slabs : 1;
+    if (mode == USPG_RESAMPLE_BIJECTION) {
+        for (int n = 1; n <= c->n_rings; n++)
+            if (c->ng[n - 1] != 8 * n - 4)
+                return fail(c, USPG_EUNSUPPORTED, "the bijective resample needs 4(2n-1) sectors per ring");
+        if (nx != 2 * c->n_rings || ny != 2 * c->n_rings)
+            return fail(c, USPG_EINVAL, "the bijective resample writes a 2N x 2N image");
+    } else if (mode != USPG_RESAMPLE_POINT) {
+        return fail(c, USPG_EINVAL, "unknown resample mode");
+    }
+    if (nx < 1 || ny < 1) return fail(c, USPG_EINVAL, "nx, ny must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = sizeof(float) * (size_t)nx * ny * ns;
+    float *dst = out;
+    if (!out_on_device) USPG_CUDA(c, cudaMallocAsync(&dst, bytes, s));
+    st = launch_resample(c, mode, nx, ny, dst, s);
+    if (st) return st;
+    if (!out_on_device) {
+        USPG_CUDA(c, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s));
+        USPG_CUDA(c, cudaFreeAsync(dst, s));
+        USPG_CUDA(c, cudaStreamSynchronize(s));
+    }
+    return USPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal definitions shared by the translation units of libuspg.
+// Nothing here is part of the C ABI (see include/uspg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <map>
+
+#include "../../include/uspg.h"
+
+namespace uspg {
+
+constexpr double kTwoPi = 6.283185307179586;  // 2*pi rounded to double
+constexpr double kNudge = 1e-12;              // counter-clockwise tie-break (rad)
+constexpr double kMinPiece = 1e-9;            // fraction of a cell dropped as a sliver
+constexpr int kMaxRings = 1024;
+constexpr int kMaxSlabs = 1024;
+constexpr int kMaxSectors = 4096;
+constexpr int kRowPad = 4;       // ray-major rows are padded to a multiple of this
+constexpr int kSlice = 32;       // cells per slice of the cell-major store
+constexpr int kMaxRing0Cross = 32;
+
+// device status bits (uspg_sync)
+constexpr int kStatusCountMismatch = 1;
+constexpr int kStatusRing0Overflow = 2;
+constexpr int kStatusBounds = 4;
+constexpr int kStatusTimeout = 8;
+
+// Stored cell index of a representative row: slab (10 b) | ring (10 b) | sector (12 b).
+__host__ __device__ inline uint32_t pack_cell(int slab, int ring, int sector)
+{
+    return (uint32_t(slab) << 22) | (uint32_t(ring) << 12) | uint32_t(sector);
+}
+__host__ __device__ inline int cell_slab(uint32_t x) { return int(x >> 22); }
+__host__ __device__ inline int cell_ring(uint32_t x) { return int((x >> 12) & 1023u); }
+__host__ __device__ inline int cell_sector(uint32_t x) { return int(x & 4095u); }
+
+// Per ring: first cell id in a slab (H_n of Eq. 2), sector count, and the
+// sector shift produced by one 1/G-turn rotation (n_g / G).
+struct RingEntry {
+    int head;
+    int ng;
+    int step;
+    int chunk0;  // first slice of this ring within a slab of the cell-major store
+};
+
+// Scan and grid geometry as the generator needs it (all by value).
+struct Geometry {
+    int geometry, n_rings, n_slabs, n_u, n_v, n_rays, n_views, weight_mode;
+    long long arc_num, arc_den;
+    double r, h, z_min, du, dv, d_so, d_sd;
+    long long cells_per_slab;
+};
+
+// View of one representative's stored rows as a kernel sees it.
+struct StoreView {
+    const long long *row_ptr;  // [n_rays + 1], absolute entry offsets
+    const uint32_t *idx;       // packed cells
+    const void *w;             // weights, stored dtype
+    const float *rowmax;       // [n_rays]
+    const long long *slice_off;   // [slices_per_rep] absolute entry offsets
+    const uint32_t *slice_meta;   // [slices_per_rep] pack_cell(slab, ring, sector0)
+    const int *slice_width;       // [slices_per_rep]
+    const uint32_t *sray;         // cell-major ray ids
+    const void *sw;               // cell-major weights
+};
+
+int64_t &launch_counter();
+
+// ---- generator (generator.cu) ----
+struct GenOut {
+    int n_reps;
+    long long nnz;      // unpadded entries
+    long long nnz_pad;  // padded ray-major entries
+    long long sell_entries;
+    long long max_row;
+};
+
+// ---- host runtime context ----
+struct Graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;
+};
+
+}  // namespace uspg
+
+struct uspg_ctx {
+    // grid
+    int n_rings = 0, sector_rule = 0, n_slabs = 1, G = 1;
+    double r = 0, h = 1, z_min = 0;
+    std::vector<int> ng, head;
+    long long cells_per_slab = 0, n_cells = 0;
+    // scan
+    uspg_scan_desc scan{};
+    int n_rays = 0;
+    // coefficient options
+    int weight_mode = USPG_LENGTH, dtype = USPG_F32;
+    double w_scale = 1.0;  // stored weight = length / w_scale
+    // view classes
+    int n_reps = 0;
+    std::vector<int> rep_view;     // view index of each representative
+    std::vector<int> rep_of_view;  // representative index of each view
+    std::vector<int> m_of_view;    // rotation of each view from its representative, in 1/G turns
+    // device tables
+    uspg::RingEntry *d_ring = nullptr;
+    double2 *d_bdir = nullptr;  // boundary directions, indexed head + j
+    int slices_per_slab = 0;
+    long long slices_per_rep = 0;
+    // store
+    bool built = false;
+    long long *d_row_ptr = nullptr;
+    uint32_t *d_idx = nullptr;
+    void *d_w = nullptr;
+    float *d_rowmax = nullptr;
+    long long *d_slice_off = nullptr;
+    uint32_t *d_slice_meta = nullptr;
+    int *d_slice_width = nullptr;
+    uint32_t *d_sray = nullptr;
+    void *d_sw = nullptr;
+    uspg::GenOut gen{};
+    // generator scratch and capacities (buffers are reused across rebuilds so
+    // that captured graphs stay valid; a reallocation clears the graph cache)
+    int *d_counts = nullptr, *d_rep_view = nullptr, *d_cell_cnt = nullptr, *d_cell_fill = nullptr;
+    long long *d_rel = nullptr;
+    double *d_w64 = nullptr;
+    size_t cap_idx = 0, cap_w = 0, cap_w64 = 0, cap_sell = 0;
+    bool store_moved = false;
+    long long nnz_all_views = 0;
+    std::vector<long long> h_row_ptr;  // host copy for get_row
+    // state
+    float *d_f = nullptr;
+    float *d_proj = nullptr;
+    bool have_proj = false;
+    float *d_res = nullptr;  // per-ray log-ratio scratch [n_rays]
+    int *d_status = nullptr;
+    int *d_sweeps = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::string, uspg::Graph> graphs;
+    int last_sweeps = 0;
+    std::string err;
+};
+
+namespace uspg {
+
+// generator.cu
+uspg_status build_store(uspg_ctx *c, cudaStream_t s);
+// mart.cu
+uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s);
+uspg_status launch_backward_view(uspg_ctx *c, int view, float lambda, cudaStream_t s);
+uspg_status launch_sequential(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s);
+StoreView store_view(const uspg_ctx *c, int rep);
+// resample.cu
+uspg_status launch_resample(uspg_ctx *c, int mode, int nx, int ny, float *out, cudaStream_t s);
+
+uspg_status fail(uspg_ctx *c, uspg_status st, const std::string &msg);
+uspg_status cuda_fail(uspg_ctx *c, cudaError_t e, const char *what);
+
+}  // namespace uspg
+
+#define USPG_CUDA(ctx, call)                                           \
+    do {                                                               \
+        cudaError_t e__ = (call);                                      \
+        if (e__ != cudaSuccess) return uspg::cuda_fail((ctx), e__, #call); \
+    } while (0)

@@ -1,0 +1,392 @@
+// MART kernels (Sec. III.D, Eq. 17-19).
+//
+// Every view k reuses the rows stored for its representative: a stored entry
+// (slab, ring, sector) of the representative becomes, in view k, cell
+// slab*C + H_ring + (sector + q) mod n_g(ring) with q = (m_k mod G) * n_g/G,
+// where m_k is the number of 1/G turns between the view and its
+// representative (Sec. III.C: rotating the source about z moves only the
+// angular position of a segment; slab and ring are unchanged).
+//
+// Per-view simultaneous schedule, two launches per view:
+//   k_forward   one warp per ray streams the ray-major row with 16-byte
+//               loads, gathers the rotated image values and reduces the ray
+//               sum with warp shuffles (Eq. 17); it stores ln(P/Pbar) per ray
+//               (-inf for P = 0, NaN for a ray that is skipped).
+//   k_backward  one warp per 32-cell slice of the cell-major store: each lane
+//               owns one cell, streams its rays and applies
+//               f *= exp(lambda * sum w ln(P/Pbar) / sum w)   (0 if any P = 0).
+//               No atomics: the store is transposed once at build time.
+// Faithful ray-sequential schedule: k_sequential, one warp that keeps the
+// image in shared memory (or global memory for large grids) and walks
+// iterations -> views -> rays in order, prefetching the next row into
+// registers while the current ray is reduced and corrected.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace uspg {
+
+int64_t &launch_counter()
+{
+    static int64_t n = 0;
+    return n;
+}
+
+StoreView store_view(const uspg_ctx *c, int rep)
+{
+    StoreView v;
+    v.row_ptr = c->d_row_ptr + (long long)rep * c->n_rays;
+    v.idx = c->d_idx;
+    v.w = c->d_w;
+    v.rowmax = c->d_rowmax + (long long)rep * c->n_rays;
+    v.slice_off = c->d_slice_off + (long long)rep * c->slices_per_rep;
+    v.slice_meta = c->d_slice_meta + (long long)rep * c->slices_per_rep;
+    v.slice_width = c->d_slice_width + (long long)rep * c->slices_per_rep;
+    v.sray = c->d_sray;
+    v.sw = c->d_sw;
+    return v;
+}
+
+// ---- weight loads ------------------------------------------------------------
+
+__device__ __forceinline__ float4 load_w4(const float *w, long long q) { return *(const float4 *)(w + q); }
+__device__ __forceinline__ float4 load_w4(const __half *w, long long q)
+{
+    uint2 u = *(const uint2 *)(w + q);
+    float2 a = __half22float2(*(const __half2 *)&u.x), b = __half22float2(*(const __half2 *)&u.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 load_w4(const __nv_bfloat16 *w, long long q)
+{
+    uint2 u = *(const uint2 *)(w + q);
+    float2 a = __bfloat1622float2(*(const __nv_bfloat162 *)&u.x), b = __bfloat1622float2(*(const __nv_bfloat162 *)&u.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float load_w1(const float *w, long long q) { return w[q]; }
+__device__ __forceinline__ float load_w1(const __half *w, long long q) { return __half2float(w[q]); }
+__device__ __forceinline__ float load_w1(const __nv_bfloat16 *w, long long q) { return __bfloat162float(w[q]); }
+
+// rotated cell id of a stored entry; tab[ring] = {head, ng, q, 0}
+__device__ __forceinline__ long long rot_cell(const int4 *tab, long long cps, uint32_t pc)
+{
+    int4 t = tab[cell_ring(pc)];
+    int s = cell_sector(pc) + t.z;
+    s = s >= t.y ? s - t.y : s;
+    return (long long)cell_slab(pc) * cps + t.x + s;
+}
+
+__device__ __forceinline__ void fill_tab(int4 *tab, const RingEntry *rt, int n_rings, int mG, int tid, int nt)
+{
+    for (int i = tid; i < n_rings; i += nt) {
+        RingEntry e = rt[i];
+        tab[i] = make_int4(e.head, e.ng, mG * e.step, 0);
+    }
+}
+
+// ---- per-view forward ----------------------------------------------------------
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_forward(const long long *__restrict__ row_ptr, const uint32_t *__restrict__ idx,
+                                                 const WT *__restrict__ w, const float *__restrict__ f,
+                                                 const RingEntry *__restrict__ rt, int n_rings, int mG, long long cps,
+                                                 const float *__restrict__ proj, int n_rays, float w_scale,
+                                                 float *__restrict__ out_s, float *__restrict__ out_res)
+{
+    extern __shared__ int4 tab[];
+    fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
+    __syncthreads();
+    int ray = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (ray >= n_rays) return;
+    long long b = row_ptr[ray], e = row_ptr[ray + 1];
+    float acc = 0.0f;
+    for (long long q = b + 4 * lane; q < e; q += 128) {
+        uint4 ix = __ldg((const uint4 *)(idx + q));
+        float4 wv = load_w4(w, q);
+        acc = fmaf(wv.x, __ldg(f + rot_cell(tab, cps, ix.x)), acc);
+        acc = fmaf(wv.y, __ldg(f + rot_cell(tab, cps, ix.y)), acc);
+        acc = fmaf(wv.z, __ldg(f + rot_cell(tab, cps, ix.z)), acc);
+        acc = fmaf(wv.w, __ldg(f + rot_cell(tab, cps, ix.w)), acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        float s = acc * w_scale;
+        if (out_s) out_s[ray] = s;
+        if (out_res) {
+            float res;
+            if (e == b || !(s > 0.0f)) {
+                res = __int_as_float(0x7fc00000);  // skip this ray
+            } else {
+                float p = proj[ray];
+                res = p > 0.0f ? logf(p / s) : -INFINITY;
+            }
+            out_res[ray] = res;
+        }
+    }
+}
+
+// ---- per-view correction (cell-major) -----------------------------------------
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_backward(const long long *__restrict__ slice_off,
+                                                  const uint32_t *__restrict__ slice_meta,
+                                                  const int *__restrict__ slice_width, const uint32_t *__restrict__ sray,
+                                                  const WT *__restrict__ sw, const float *__restrict__ res,
+                                                  float *__restrict__ f, const RingEntry *__restrict__ rt, int mG,
+                                                  long long cps, long long n_slices, float lambda)
+{
+    long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (sl >= n_slices) return;
+    uint32_t meta = slice_meta[sl];
+    int width = slice_width[sl];
+    long long off = slice_off[sl] + lane;
+    float num = 0.0f, den = 0.0f;
+    bool zero = false;
+    for (int t = 0; t < width; t++) {
+        long long pos = off + (long long)t * kSlice;
+        uint32_t ray = __ldg(sray + pos);
+        float wv = load_w1(sw, pos);
+        float r = __ldg(res + ray);
+        bool act = (wv > 0.0f) && (r == r);
+        bool zr = act && (r == -INFINITY);
+        den += act ? wv : 0.0f;
+        zero |= zr;
+        num += (act && !zr) ? wv * r : 0.0f;
+    }
+    int ring = cell_ring(meta);
+    RingEntry re = rt[ring];
+    int sec = cell_sector(meta) + lane;
+    if (sec < re.ng && den > 0.0f) {
+        int s2 = sec + mG * re.step;
+        s2 = s2 >= re.ng ? s2 - re.ng : s2;
+        long long cell = (long long)cell_slab(meta) * cps + re.head + s2;
+        f[cell] = zero ? 0.0f : f[cell] * expf(lambda * (num / den));
+    }
+}
+
+template <typename WT>
+static uspg_status fwd_typed(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s)
+{
+    int rep = c->rep_of_view[view];
+    int mG = c->m_of_view[view] % c->G;
+    StoreView v = store_view(c, rep);
+    const int TB = 256;
+    unsigned grid = (unsigned)(((long long)c->n_rays * 32 + TB - 1) / TB);
+    size_t smem = sizeof(int4) * c->n_rings;
+    k_forward<WT><<<grid, TB, smem, s>>>(v.row_ptr, v.idx, (const WT *)v.w, c->d_f, c->d_ring, c->n_rings, mG,
+                                         c->cells_per_slab, c->d_proj + (long long)view * c->n_rays, c->n_rays,
+                                         (float)c->w_scale, out_s, out_res);
+    launch_counter()++;
+    USPG_CUDA(c, cudaGetLastError());
+    return USPG_OK;
+}
+
+uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s)
+{
+    if (c->dtype == USPG_F16) return fwd_typed<__half>(c, view, out_s, out_res, s);
+    if (c->dtype == USPG_BF16) return fwd_typed<__nv_bfloat16>(c, view, out_s, out_res, s);
+    return fwd_typed<float>(c, view, out_s, out_res, s);
+}
+
+template <typename WT>
+static uspg_status bwd_typed(uspg_ctx *c, int view, float lambda, cudaStream_t s)
+{
+    int rep = c->rep_of_view[view];
+    int mG = c->m_of_view[view] % c->G;
+    StoreView v = store_view(c, rep);
+    const int TB = 256;
+    unsigned grid = (unsigned)((c->slices_per_rep * 32 + TB - 1) / TB);
+    k_backward<WT><<<grid, TB, 0, s>>>(v.slice_off, v.slice_meta, v.slice_width, v.sray, (const WT *)v.sw, c->d_res,
+                                       c->d_f, c->d_ring, mG, c->cells_per_slab, c->slices_per_rep, lambda);
+    launch_counter()++;
+    USPG_CUDA(c, cudaGetLastError());
+    return USPG_OK;
+}
+
+uspg_status launch_backward_view(uspg_ctx *c, int view, float lambda, cudaStream_t s)
+{
+    if (c->dtype == USPG_F16) return bwd_typed<__half>(c, view, lambda, s);
+    if (c->dtype == USPG_BF16) return bwd_typed<__nv_bfloat16>(c, view, lambda, s);
+    return bwd_typed<float>(c, view, lambda, s);
+}
+
+// ---- faithful ray-sequential MART -----------------------------------------------
+
+constexpr int kSeqChunks = 8;  // rows up to 256 entries live in registers
+
+template <typename WT>
+struct RowRegs {
+    uint32_t ix[kSeqChunks];
+    float w[kSeqChunks];
+};
+
+template <typename WT>
+__device__ __forceinline__ void seq_load(RowRegs<WT> &R, const uint32_t *idx, const WT *w, long long b, long long e,
+                                         int lane)
+{
+#pragma unroll
+    for (int c = 0; c < kSeqChunks; c++) {
+        long long q = b + c * 32 + lane;
+        if (q < e) {
+            R.ix[c] = __ldg(idx + q);
+            R.w[c] = load_w1(w, q);
+        } else {
+            R.ix[c] = 0;
+            R.w[c] = 0.0f;
+        }
+    }
+}
+
+// One warp.  f in shared memory when SMEM, else in global memory.
+template <typename WT, bool SMEM>
+__global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__ row_ptr_all,
+                                                   const uint32_t *__restrict__ idx, const WT *__restrict__ w,
+                                                   const float *__restrict__ rowmax_all,
+                                                   const int *__restrict__ view_rep, const int *__restrict__ view_mg,
+                                                   int n_views, int n_rays, const float *__restrict__ proj,
+                                                   float *f_g, long long n_cells, const RingEntry *__restrict__ rt,
+                                                   int n_rings, long long cps, int iters, float lambda, int rule,
+                                                   float tol, float w_scale, int *sweeps_out)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = (float *)smem4;
+    const int lane = threadIdx.x;
+    long long fcells = SMEM ? ((n_cells + 3) & ~3LL) : 0;
+    float *fs = SMEM ? sm : f_g;
+    int4 *tab = (int4 *)(sm + fcells);
+    if (SMEM) {
+        for (long long q = lane; q < n_cells; q += 32) fs[q] = f_g[q];
+    }
+    __syncwarp();
+    int it = 0;
+    for (; it < iters; it++) {
+        int changed = 0;
+        for (int k = 0; k < n_views; k++) {
+            int rep = view_rep[k];
+            fill_tab(tab, rt, n_rings, view_mg[k], lane, 32);
+            __syncwarp();
+            const long long *rp = row_ptr_all + (long long)rep * n_rays;
+            const float *rmax = rowmax_all + (long long)rep * n_rays;
+            const float *pk = proj + (long long)k * n_rays;
+            RowRegs<WT> cur, nxt;
+            long long cb = rp[0], ce = rp[1];
+            seq_load(cur, idx, w, cb, ce, lane);
+            for (int ray = 0; ray < n_rays; ray++) {
+                long long nb = ce, ne = ce;
+                if (ray + 1 < n_rays) {
+                    ne = rp[ray + 2];
+                    seq_load(nxt, idx, w, nb, ne, lane);
+                }
+                if (ce > cb) {
+                    float acc = 0.0f;
+                    long long cell[kSeqChunks];
+#pragma unroll
+                    for (int c = 0; c < kSeqChunks; c++) {
+                        cell[c] = rot_cell(tab, cps, cur.ix[c]);
+                        acc = fmaf(cur.w[c], fs[cell[c]], acc);
+                    }
+                    for (long long q = cb + kSeqChunks * 32 + lane; q < ce; q += 32)  // long rows
+                        acc = fmaf(load_w1(w, q), fs[rot_cell(tab, cps, __ldg(idx + q))], acc);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    float s = acc * w_scale;
+                    if (s > 0.0f) {
+                        float ratio = pk[ray] / s;
+                        float l2 = log2f(ratio);
+                        float ex = lambda / rmax[ray];
+                        float lin = 1.0f - lambda * (1.0f - ratio);
+#pragma unroll
+                        for (int c = 0; c < kSeqChunks; c++) {
+                            if (cur.w[c] > 0.0f) {
+                                float old = fs[cell[c]];
+                                float fac = rule == USPG_LINEAR_EQ18 ? lin : exp2f(ex * cur.w[c] * l2);
+                                float nv = old * fac;
+                                if (tol > 0.0f && fabsf(nv - old) > tol * fabsf(old)) changed = 1;
+                                fs[cell[c]] = nv;
+                            }
+                        }
+                        for (long long q = cb + kSeqChunks * 32 + lane; q < ce; q += 32) {
+                            float wv = load_w1(w, q);
+                            if (wv > 0.0f) {
+                                long long cl = rot_cell(tab, cps, __ldg(idx + q));
+                                float old = fs[cl];
+                                float fac = rule == USPG_LINEAR_EQ18 ? lin : exp2f(ex * wv * l2);
+                                float nv = old * fac;
+                                if (tol > 0.0f && fabsf(nv - old) > tol * fabsf(old)) changed = 1;
+                                fs[cl] = nv;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (!SMEM) __threadfence_block();
+                }
+                cur = nxt;
+                cb = nb;
+                ce = ne;
+            }
+            __syncwarp();
+        }
+        if (tol > 0.0f) {
+            if (!__any_sync(0xffffffffu, changed)) {
+                it++;
+                break;
+            }
+        }
+    }
+    if (SMEM) {
+        __syncwarp();
+        for (long long q = lane; q < n_cells; q += 32) f_g[q] = fs[q];
+    }
+    if (lane == 0 && sweeps_out) *sweeps_out = it;
+}
+
+template <typename WT>
+static uspg_status seq_typed(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s)
+{
+    int nv = c->scan.n_views;
+    std::vector<int> vr(nv), vm(nv);
+    for (int k = 0; k < nv; k++) {
+        vr[k] = c->rep_of_view[k];
+        vm[k] = c->m_of_view[k] % c->G;
+    }
+    int *d_v = nullptr;
+    USPG_CUDA(c, cudaMallocAsync(&d_v, sizeof(int) * 2 * nv, s));
+    USPG_CUDA(c, cudaMemcpyAsync(d_v, vr.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, s));
+    USPG_CUDA(c, cudaMemcpyAsync(d_v + nv, vm.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, s));
+    size_t tab_bytes = sizeof(int4) * c->n_rings;
+    size_t f_bytes = sizeof(float) * ((c->n_cells + 3) & ~3LL);
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    bool use_smem = f_bytes + tab_bytes <= (size_t)max_smem;
+    float tol = (float)o->stop_tol;
+    if (use_smem) {
+        size_t sm = f_bytes + tab_bytes;
+        USPG_CUDA(c, cudaFuncSetAttribute(k_sequential<WT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_sequential<WT, true><<<1, 32, sm, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v, d_v + nv,
+                                                 nv, c->n_rays, c->d_proj, c->d_f, c->n_cells, c->d_ring, c->n_rings,
+                                                 c->cells_per_slab, o->iterations, (float)o->lambda, o->update_rule, tol,
+                                                 (float)c->w_scale, c->d_sweeps);
+    } else {
+        k_sequential<WT, false><<<1, 32, tab_bytes, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v,
+                                                         d_v + nv, nv, c->n_rays, c->d_proj, c->d_f, c->n_cells,
+                                                         c->d_ring, c->n_rings, c->cells_per_slab, o->iterations,
+                                                         (float)o->lambda, o->update_rule, tol, (float)c->w_scale,
+                                                         c->d_sweeps);
+    }
+    launch_counter()++;
+    USPG_CUDA(c, cudaGetLastError());
+    USPG_CUDA(c, cudaFreeAsync(d_v, s));
+    return USPG_OK;
+}
+
+uspg_status launch_sequential(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s)
+{
+    if (c->dtype == USPG_F16) return seq_typed<__half>(c, o, s);
+    if (c->dtype == USPG_BF16) return seq_typed<__nv_bfloat16>(c, o, s);
+    return seq_typed<float>(c, o, s);
+}
+
+}  // namespace uspg

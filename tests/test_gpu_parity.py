@@ -1,0 +1,250 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: cell index lists bit-exact; stored FP32 weights within 1e-6 relative;
+MART images within 1e-4 relative L2 of the FP64 oracle after the stated
+iterations; resampled images exact (the resample is a gather of FP32 image
+values, the cell choice is an integer decision taken in FP64 on both sides).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import Gpu, assert_rows_equal, oracle_for, rel_l2
+from paper_2208_12964_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_W = 1e-6
+TOL_IMG = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available()
+    return torch
+
+
+# -------------------------------------------------------------- generator ---
+
+def test_rows_2d_parallel_all_views_all_rays(torch_cuda):
+    spec = synth.workload("2d-parallel-64r-36v")
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    st = g.stats()
+    assert st["n_reps"] == 12 and st["n_cells"] == 12480 and st["gcd"] == 6
+    total = 0
+    for k in range(36):
+        for b in range(65):
+            gc, gw = g.row(k, b)
+            oc, ow = o.row(k, b)
+            assert_rows_equal(gc, gw, oc, ow, TOL_W, where=f"view {k} ray {b}")
+            total += len(oc)
+    assert total == st["nnz_all_views"]
+
+
+@pytest.mark.parametrize("case", ["6n", "4_2n1", "custom"])
+def test_rows_3d_cone_small_all_rays(torch_cuda, case):
+    spec = synth.cone_workload(12, 8, 18, 24, noise=False)
+    if case == "4_2n1":
+        spec["sector_rule"] = synth.SECT_4_2N1
+    elif case == "custom":
+        spec["sector_rule"] = synth.SECT_CUSTOM
+        spec["custom_sectors"] = [5, 9, 12, 14, 20, 22, 27, 30, 33, 40, 41, 48]
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    for k in range(18):
+        for ray in range(24 * 24):
+            gc, gw = g.row(k, ray)
+            oc, ow = o.row(k, ray)
+            assert_rows_equal(gc, gw, oc, ow, TOL_W, where=f"{case} view {k} ray {ray}")
+
+
+def test_rows_3d_cone_full_size_sampled(torch_cuda):
+    """The 128-ring, 128-slab, 90-view, 256x256 workload: 400 sampled rows
+    (oracle traces each one directly)."""
+    spec = synth.workload("3d-cone-128r-128s-90v-256")
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    st = g.stats()
+    assert st["n_reps"] == 15 and st["n_cells"] == 6340608
+    rng = np.random.default_rng(7)
+    for _ in range(400):
+        k = int(rng.integers(90))
+        ray = int(rng.integers(256 * 256))
+        gc, gw = g.row(k, ray)
+        oc, ow = o.row(k, ray)
+        assert_rows_equal(gc, gw, oc, ow, TOL_W, where=f"view {k} ray {ray}")
+
+
+def test_binary_weights(torch_cuda):
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.parallel_workload(9, 10, 19)
+    g = Gpu(spec, weight_mode=uspg.BINARY).build()
+    o = oracle_for(spec, weight_mode=1)
+    for k in range(10):
+        for b in range(19):
+            gc, gw = g.row(k, b)
+            oc, ow = o.row(k, b)
+            assert np.array_equal(gc, oc) and np.all(gw == 1.0)
+
+
+# ---------------------------------------------------------------- forward ---
+
+def test_forward_projection_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    spec = synth.cone_workload(10, 6, 12, 20, noise=False)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    rng = np.random.default_rng(3)
+    f = (0.2 + rng.random(o.n_cells)).astype(np.float32)
+    g.U.uspg_set_image(g.ctx, f, False)
+    out = torch.zeros(o.n_rays, dtype=torch.float32, device="cuda")
+    for k in range(12):
+        g.U.uspg_forward_project(g.ctx, k, out)
+        g.U.uspg_sync(g.ctx)
+        ref = o.forward(k, f.astype(np.float64))
+        got = out.cpu().numpy().astype(np.float64)
+        hit = ref > 0
+        assert np.all(got[~hit] == 0.0)
+        assert np.max(np.abs(got[hit] - ref[hit]) / ref[hit]) < 2e-6
+
+
+# ------------------------------------------------------------------- MART ---
+
+def _run_mart(g, proj, f0, iters, lam, schedule, rule=0, order=None, tol=0.0):
+    U = g.U
+    U.uspg_set_projections(g.ctx, np.ascontiguousarray(proj, np.float32), False)
+    U.uspg_set_image(g.ctx, np.ascontiguousarray(f0, np.float32), False)
+    o, keep = U.mart_opts(iters, lam, schedule, rule, tol, order)
+    U.uspg_mart(g.ctx, o)
+    U.uspg_sync(g.ctx)
+    f = np.zeros(len(f0), np.float32)
+    U.uspg_get_image(g.ctx, f, False)
+    return f
+
+
+def test_mart_sequential_2d_workload(torch_cuda):
+    """The 64-ring, 36-view parallel workload, 10 ray-sequential iterations,
+    lambda 0.2, f0 = 1 (the paper's ray order)."""
+    spec = synth.workload("2d-parallel-64r-36v")
+    proj = synth.projections(spec)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    f0 = np.ones(o.n_cells)
+    ref, _ = o.mart_sequential(proj, f0, 10, 0.2)
+    got = _run_mart(g, proj, f0, 10, 0.2, 0)
+    assert rel_l2(got, ref) < TOL_IMG
+    assert np.all(got >= 0)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_mart_sequential_rules_and_stop(torch_cuda, rule):
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.parallel_workload(12, 18, 25, seed=5)
+    proj = synth.projections(spec)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    f0 = np.ones(o.n_cells)
+    ref, _ = o.mart_sequential(proj, f0, 4, 0.3, rule=rule)
+    got = _run_mart(g, proj, f0, 4, 0.3, 0, rule=rule)
+    assert rel_l2(got, ref) < TOL_IMG
+    # Eq. 19: consistent data from the oracle's own forward projection
+    fstar = 0.5 + np.random.default_rng(1).random(o.n_cells)
+    p = np.stack([o.forward(k, fstar) for k in range(18)]).astype(np.float32)
+    _run_mart(g, p, fstar, 30, 0.3, 0, rule=rule, tol=1e-3)
+    assert uspg.uspg_mart_sweeps(g.ctx) == 1
+
+
+def test_mart_per_view_3d_noisy(torch_cuda):
+    spec = synth.cone_workload(16, 12, 24, 32, iterations=3, lam=0.1, seed=9)
+    proj = synth.projections(spec)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    f0 = np.ones(o.n_cells)
+    ref = o.mart_per_view(proj, f0, 3, 0.1)
+    got = _run_mart(g, proj, f0, 3, 0.1, 1)
+    assert rel_l2(got, ref) < TOL_IMG
+    assert np.all(got >= 0) and np.any(got == 0)  # noisy zero rays zero their cells
+
+
+def test_mart_per_view_2d_custom_order(torch_cuda):
+    spec = synth.parallel_workload(40, 30, 81, seed=4)
+    proj = synth.projections(spec)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    order = np.random.default_rng(2).permutation(30)
+    f0 = np.ones(o.n_cells)
+    ref = o.mart_per_view(proj, f0, 4, 0.3, order=order)
+    got = _run_mart(g, proj, f0, 4, 0.3, 1, order=order)
+    assert rel_l2(got, ref) < TOL_IMG
+
+
+# --------------------------------------------------------------- resample ---
+
+def test_resample_point_and_bijection(torch_cuda):
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.parallel_workload(16, 4, 33, sector_rule=synth.SECT_4_2N1)
+    g = Gpu(spec)
+    o = oracle_for(spec)
+    f = np.random.default_rng(0).random(o.n_cells).astype(np.float32)
+    uspg.uspg_set_image(g.ctx, f, False)
+    for nx, ny in ((64, 64), (37, 53), (1, 1)):
+        out = np.zeros((1, ny, nx), np.float32)
+        uspg.uspg_resample_cartesian(g.ctx, uspg.RESAMPLE_POINT, nx, ny, out, False)
+        ref = o.resample_point(f.astype(np.float64), nx, ny)
+        assert np.array_equal(out, ref.astype(np.float32))
+    out = np.zeros((1, 32, 32), np.float32)
+    uspg.uspg_resample_cartesian(g.ctx, uspg.RESAMPLE_BIJECTION, 32, 32, out, False)
+    assert np.array_equal(out, o.resample_bijection(f.astype(np.float64)).astype(np.float32))
+
+
+def test_resample_3d_slabs(torch_cuda):
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.cone_workload(8, 5, 6, 16, noise=False)
+    g = Gpu(spec)
+    o = oracle_for(spec)
+    f = np.random.default_rng(1).random(o.n_cells).astype(np.float32)
+    uspg.uspg_set_image(g.ctx, f, False)
+    out = np.zeros((5, 24, 24), np.float32)
+    uspg.uspg_resample_cartesian(g.ctx, uspg.RESAMPLE_POINT, 24, 24, out, False)
+    assert np.array_equal(out, o.resample_point(f.astype(np.float64), 24, 24).astype(np.float32))
+
+
+# ------------------------------------------------------------- edge cases ---
+
+def test_errors_and_degenerate_inputs(torch_cuda):
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.parallel_workload(4, 3, 9)
+    g = Gpu(spec)
+    o, _ = uspg.mart_opts(1, 0.5, uspg.PER_VIEW)
+    with pytest.raises(uspg.UspgError) as e:
+        uspg.uspg_mart(g.ctx, o)
+    assert e.value.status == uspg.ENOTREADY
+    g.build()
+    with pytest.raises(uspg.UspgError):
+        uspg.uspg_mart(g.ctx, uspg.mart_opts(1, 2.5, uspg.PER_VIEW)[0])
+    bad = dict(spec, n_rings=0)
+    with pytest.raises(uspg.UspgError) as e:
+        Gpu(bad)
+    assert e.value.status == uspg.EINVAL
+    # detector wider than the disk: outer rays miss and keep empty rows
+    wide = synth.parallel_workload(4, 3, 9)
+    wide["du"] = 0.5
+    gw = Gpu(wide).build()
+    ow = oracle_for(wide)
+    for k in range(3):
+        for b in range(9):
+            gc, gwt = gw.row(k, b)
+            oc, owt = ow.row(k, b)
+            assert_rows_equal(gc, gwt, oc, owt, TOL_W)
+    assert len(gw.row(0, 0)[0]) == 0
+    # zero iterations leave the image unchanged
+    f0 = np.full(ow.n_cells, 0.7, np.float32)
+    got = _run_mart(gw, np.ones((3, 9), np.float32), f0, 0, 0.5, 1)
+    assert np.array_equal(got, f0)
