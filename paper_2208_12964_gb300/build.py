@@ -3,7 +3,8 @@
 ``python -m paper_2208_12964_gb300.build`` compiles each translation unit with
 nvcc in parallel and links ``_lib/libuspg.so``.  The generator is compiled
 with ``-fmad=false`` so its FP64 crossings are formed with separately rounded
-operations.
+operations; so is the resample, whose pixel-centre classification follows the
+same rule.
 """
 from __future__ import annotations
 
@@ -23,7 +24,7 @@ UNITS = {
     "api.cu": [],
     "generator.cu": ["-fmad=false"],
     "mart.cu": [],
-    "resample.cu": [],
+    "resample.cu": ["-fmad=false"],
 }
 
 

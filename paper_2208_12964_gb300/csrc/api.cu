@@ -53,9 +53,11 @@ static void free_store(uspg_ctx *c)
     cudaFree(c->d_cell_cnt);
     cudaFree(c->d_cell_fill);
     cudaFree(c->d_rel);
+    cudaFree(c->d_stats);
     cudaFree(c->d_w64);
     c->d_counts = c->d_rep_view = c->d_cell_cnt = c->d_cell_fill = nullptr;
     c->d_rel = nullptr;
+    c->d_stats = nullptr;
     c->d_w64 = nullptr;
     c->cap_idx = c->cap_w = c->cap_w64 = c->cap_sell = 0;
     c->d_row_ptr = nullptr;
@@ -239,6 +241,7 @@ void uspg_destroy(uspg_ctx *c)
     free_store(c);
     cudaFree(c->d_ring);
     cudaFree(c->d_bdir);
+    cudaFree(c->d_bdirf);
     cudaFree(c->d_f);
     cudaFree(c->d_proj);
     cudaFree(c->d_res);
@@ -323,6 +326,12 @@ uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t 
     if (view < 0 || view >= c->scan.n_views || ray < 0 || ray >= c->n_rays) return fail(c, USPG_EINVAL, "bad view/ray");
     int rep = c->rep_of_view[view];
     long long row = (long long)rep * c->n_rays + ray;
+    if (c->h_row_ptr.empty()) {
+        long long nrows = (long long)c->n_reps * c->n_rays;
+        c->h_row_ptr.resize(nrows + 1);
+        USPG_CUDA(c, cudaMemcpy(c->h_row_ptr.data(), c->d_row_ptr, sizeof(long long) * (nrows + 1),
+                                cudaMemcpyDeviceToHost));
+    }
     long long b = c->h_row_ptr[row], e = c->h_row_ptr[row + 1];
     std::vector<uint32_t> ix(e - b);
     int wb = c->dtype == USPG_F32 ? 4 : 2;

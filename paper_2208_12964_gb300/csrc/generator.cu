@@ -21,415 +21,142 @@
 // -> cell-major store (count per cell, slice widths, scan, scatter, per-cell
 // sort by ray id so the layout is deterministic).
 #include "internal.cuh"
+#include "walk.cuh"
 
 #include <algorithm>
 
 namespace uspg {
 
-__device__ __forceinline__ void ray_endpoints(const Geometry &g, int k, int ray, double S[3], double D[3])
-{
-    double frac = (double)((long long)k * g.arc_num) / (double)(g.arc_den * (long long)g.n_views);
-    double th = kTwoPi * frac;
-    double ct = cos(th), st = sin(th);
-    if (g.geometry == USPG_PARALLEL_2D) {
-        double R = (double)g.n_rings * g.r;
-        double u = (double)(2 * ray - (g.n_u - 1)) * (0.5 * g.du);
-        double eux = ct, euy = st, erx = -st, ery = ct;
-        double L = 2.0 * R;
-        S[0] = u * eux - L * erx;
-        S[1] = u * euy - L * ery;
-        S[2] = 0.0;
-        D[0] = u * eux + L * erx;
-        D[1] = u * euy + L * ery;
-        D[2] = 0.0;
-    } else {
-        int a = ray % g.n_u, c = ray / g.n_u;
-        double u = (double)(2 * a - (g.n_u - 1)) * (0.5 * g.du);
-        double v = (double)(2 * c - (g.n_v - 1)) * (0.5 * g.dv);
-        double off = g.d_sd - g.d_so;
-        S[0] = -g.d_so * ct;
-        S[1] = -g.d_so * st;
-        S[2] = 0.0;
-        D[0] = off * ct + u * (-st);
-        D[1] = off * st + u * ct;
-        D[2] = v;
-    }
-}
-
-// Per-ray tracing state shared by the segment walks.
-struct Ray {
-    double S[3], dx, dy, dz, L, a, t, d, lo, hi, min_len, sigma;
-};
-
-struct CountSink {
-    int n = 0;
-    uint32_t last = 0xffffffffu;
-    __device__ void emit(uint32_t cell, double)
-    {
-        if (n > 0 && cell == last) return;
-        last = cell;
-        n++;
-    }
-};
-
-struct FillSink {
-    uint32_t *idx;
-    double *w;
-    int n = 0;
-    int cap = 0;
-    uint32_t last = 0xffffffffu;
-    int overflow = 0;
-    __device__ void emit(uint32_t cell, double len)
-    {
-        if (n > 0 && cell == last) {
-            w[n - 1] += len;
-            return;
-        }
-        if (n >= cap) {
-            overflow = 1;
-            return;
-        }
-        idx[n] = cell;
-        w[n] = len;
-        last = cell;
-        n++;
-    }
-};
-
-// Classify the piece [la, lb] by its midpoint (Eq. 5-10) and emit it.
-template <class Sink>
-__device__ __forceinline__ void piece(const Geometry &g, const RingEntry *rt, const Ray &R, double la, double lb,
-                                      Sink &sink)
-{
-    double len = (lb - la) * R.L;
-    if (!(len >= R.min_len)) return;
-    double pax = R.S[0] + la * R.dx, pay = R.S[1] + la * R.dy, paz = R.S[2] + la * R.dz;
-    double pbx = R.S[0] + lb * R.dx, pby = R.S[1] + lb * R.dy, pbz = R.S[2] + lb * R.dz;
-    double mx = 0.5 * (pax + pbx), my = 0.5 * (pay + pby), mz = 0.5 * (paz + pbz);
-    double rho = sqrt(mx * mx + my * my);
-    long long ring = (long long)floor(rho / g.r);
-    if (ring < 0) ring = 0;
-    if (ring > g.n_rings - 1) ring = g.n_rings - 1;
-    long long slab = 0;
-    if (g.geometry == USPG_CONE_3D) {
-        slab = (long long)floor((mz - g.z_min) / g.h);
-        if (slab < 0) slab = 0;
-        if (slab > g.n_slabs - 1) slab = g.n_slabs - 1;
-    }
-    int ng = rt[ring].ng;
-    double phi = atan2(my, mx);
-    if (phi < 0.0) phi += kTwoPi;
-    long long sec = (long long)floor(((phi + kNudge) * (double)ng) / kTwoPi);
-    if (sec >= ng) sec -= ng;
-    if (sec < 0) sec = 0;
-    sink.emit(pack_cell((int)slab, (int)ring, (int)sec), len);
-}
-
-// Axial-plane crossings inside (sa, sb), in ascending parameter order.
-struct ZStream {
-    int s, s_end, step;  // candidate plane indices
-    double next;
-    __device__ void init(const Geometry &g, const Ray &R, double sa, double sb)
-    {
-        next = 2.0;
-        if (g.geometry != USPG_CONE_3D || R.dz == 0.0) {
-            s = 0;
-            s_end = 0;
-            step = 1;
-            return;
-        }
-        double za = R.S[2] + sa * R.dz, zb = R.S[2] + sb * R.dz;
-        int ia = (int)floor((za - g.z_min) / g.h), ib = (int)floor((zb - g.z_min) / g.h);
-        if (R.dz > 0.0) {
-            s = ia;
-            s_end = ib + 2;
-            step = 1;
-        } else {
-            s = ia + 1;
-            s_end = ib - 1;
-            step = -1;
-        }
-        // candidates can only lie in [0, n_slabs]; keep the loop bounded
-        int span = (s_end - s) * step;
-        if (!(span >= 0 && span <= g.n_slabs + 3)) {
-            s = 0;
-            s_end = 0;
-        }
-    }
-    __device__ void advance(const Geometry &g, const Ray &R, double sa, double sb)
-    {
-        next = 2.0;
-        while (s != s_end) {
-            int cs = s;
-            s += step;
-            if (cs < 1 || cs > g.n_slabs - 1) continue;
-            double zs = g.z_min + (double)cs * g.h;
-            double l = (zs - R.S[2]) / R.dz;
-            if (l > sa && l < sb) {
-                next = l;
-                return;
-            }
-        }
-    }
-};
-
-// Radial-plane crossings of ring i inside (sa, sb), ascending, for i >= 1:
-// candidates are the boundaries between the azimuths of the segment ends
-// (one extra on each side), each accepted by the exact test.
-struct RStream {
-    long long j, j_end;
-    int dir, i, ng, head;
-    double rin, rout, next;
-    __device__ void init(const Geometry &g, const RingEntry *rt, const Ray &R, int ring, double sa, double sb)
-    {
-        i = ring;
-        ng = rt[ring].ng;
-        head = rt[ring].head;
-        rin = (double)ring * g.r;
-        rout = (double)(ring + 1) * g.r;
-        next = 2.0;
-        double xa = R.S[0] + sa * R.dx, ya = R.S[1] + sa * R.dy;
-        double xb = R.S[0] + sb * R.dx, yb = R.S[1] + sb * R.dy;
-        double fa = atan2(ya, xa), fb = atan2(yb, xb);
-        if (fa < 0.0) fa += kTwoPi;
-        if (fb < 0.0) fb += kTwoPi;
-        double scale = (double)ng / kTwoPi;
-        if (R.sigma > 0.0) {  // azimuth grows along the ray
-            if (fb < fa) fb += kTwoPi;
-            j = (long long)floor(fa * scale);
-            j_end = (long long)floor(fb * scale) + 2;
-            dir = 1;
-        } else if (R.sigma < 0.0) {
-            if (fb > fa) fb -= kTwoPi;
-            j = (long long)floor(fa * scale) + 1;
-            j_end = (long long)floor(fb * scale) - 1;
-            dir = -1;
-        } else {  // the ray meets the axis: the segment is radial
-            j = (long long)floor(fa * scale) - 1;
-            j_end = j + 3;
-            dir = 1;
-        }
-        // at most one lap of candidates (plus the margins)
-        long long span = (j_end - j) * dir;
-        if (!(span >= 0 && span <= (long long)ng + 3)) {
-            j = 0;
-            j_end = ng;
-            dir = 1;
-        }
-    }
-    __device__ void advance(const Ray &R, const double2 *bdir, double sa, double sb)
-    {
-        next = 2.0;
-        while (j != j_end) {
-            long long jj = j % ng;
-            if (jj < 0) jj += ng;
-            j += dir;
-            double2 e = bdir[head + jj];
-            double cj = e.x, sj = e.y;
-            double den = R.dx * sj - R.dy * cj;
-            if (den == 0.0) continue;
-            double num = R.S[0] * sj - R.S[1] * cj;
-            double l = -num / den;
-            if (!(l > sa && l < sb)) continue;
-            if (!(l > R.lo && l < R.hi)) continue;
-            double px = R.S[0] + l * R.dx, py = R.S[1] + l * R.dy;
-            double rho = px * cj + py * sj;
-            if (rho >= rin && rho <= rout) {
-                next = l;
-                return;
-            }
-        }
-    }
-};
-
-// Walk the ring-i segment [sa, sb] (already clipped) and emit its pieces.
-template <class Sink>
-__device__ void walk_segment(const Geometry &g, const RingEntry *rt, const double2 *bdir, const Ray &R, int ring,
-                             double sa, double sb, Sink &sink, int *status)
-{
-    if (!(sb > sa)) return;
-    ZStream zs;
-    zs.init(g, R, sa, sb);
-    zs.advance(g, R, sa, sb);
-    double prev = sa;
-    if (ring == 0) {
-        // all sectors of ring 0 meet on the axis: test every boundary and the
-        // closest-approach point, then sort the few accepted crossings
-        double xs[kMaxRing0Cross];
-        int nx = 0;
-        int ng = rt[0].ng;
-        double rout = g.r;
-        for (int jj = 0; jj < ng; jj++) {
-            double2 e = bdir[jj];
-            double den = R.dx * e.y - R.dy * e.x;
-            if (den == 0.0) continue;
-            double num = R.S[0] * e.y - R.S[1] * e.x;
-            double l = -num / den;
-            if (!(l > sa && l < sb)) continue;
-            if (!(l > R.lo && l < R.hi)) continue;
-            double px = R.S[0] + l * R.dx, py = R.S[1] + l * R.dy;
-            double rho = px * e.x + py * e.y;
-            if (rho >= 0.0 && rho <= rout) {
-                if (nx < kMaxRing0Cross) xs[nx++] = l;
-                else atomicOr(status, kStatusRing0Overflow);
-            }
-        }
-        if (R.d < g.r && R.t > sa && R.t < sb) {
-            if (nx < kMaxRing0Cross) xs[nx++] = R.t;
-            else atomicOr(status, kStatusRing0Overflow);
-        }
-        for (int q = 1; q < nx; q++) {  // insertion sort
-            double v = xs[q];
-            int p = q - 1;
-            while (p >= 0 && xs[p] > v) {
-                xs[p + 1] = xs[p];
-                p--;
-            }
-            xs[p + 1] = v;
-        }
-        int q = 0;
-        for (;;) {
-            double rn = q < nx ? xs[q] : 2.0;
-            double nxt = rn < zs.next ? rn : zs.next;
-            if (!(nxt < sb)) break;
-            if (nxt > prev) {
-                piece(g, rt, R, prev, nxt, sink);
-                prev = nxt;
-            }
-            if (rn <= zs.next) q++;
-            else zs.advance(g, R, sa, sb);
-        }
-    } else {
-        RStream rs;
-        rs.init(g, rt, R, ring, sa, sb);
-        rs.advance(R, bdir, sa, sb);
-        for (;;) {
-            double nxt = rs.next < zs.next ? rs.next : zs.next;
-            if (!(nxt < sb)) break;
-            if (nxt > prev) {
-                piece(g, rt, R, prev, nxt, sink);
-                prev = nxt;
-            }
-            if (rs.next <= zs.next) rs.advance(R, bdir, sa, sb);
-            else zs.advance(g, R, sa, sb);
-        }
-    }
-    if (sb > prev) piece(g, rt, R, prev, sb, sink);
-}
-
-__device__ __forceinline__ double root_k(double m, double r, double d, double a)
-{
-    double rm = m * r;
-    return sqrt(((rm - d) * (rm + d)) / a);
-}
-
-// Full walk of one ray: set-up per Eq. 3-4, then ring segments.
-template <class Sink>
-__device__ void walk_ray(const Geometry &g, const RingEntry *rt, const double2 *bdir, int view, int ray, Sink &sink,
-                         int *status)
-{
-    Ray R;
-    double D[3];
-    ray_endpoints(g, view, ray, R.S, D);
-    R.dx = D[0] - R.S[0];
-    R.dy = D[1] - R.S[1];
-    R.dz = D[2] - R.S[2];
-    R.L = sqrt(R.dx * R.dx + R.dy * R.dy + R.dz * R.dz);
-    double unit = g.r;
-    if (g.geometry == USPG_CONE_3D && g.h < unit) unit = g.h;
-    R.min_len = kMinPiece * unit;
-    double ax = R.S[0], ay = R.S[1];
-    R.a = R.dx * R.dx + R.dy * R.dy;
-    if (R.a == 0.0) return;
-    R.t = -(ax * R.dx + ay * R.dy) / R.a;
-    double d2 = (ax * ax + ay * ay) - R.t * R.t * R.a;
-    if (d2 < 0.0) d2 = 0.0;
-    R.d = sqrt(d2);
-    const int N = g.n_rings;
-    double Rc = (double)N * g.r;
-    if (!(R.d < Rc)) return;
-    double kR = sqrt(((Rc - R.d) * (Rc + R.d)) / R.a);
-    double lo = R.t - kR, hi = R.t + kR;
-    if (lo < 0.0) lo = 0.0;
-    if (hi > 1.0) hi = 1.0;
-    if (g.geometry == USPG_CONE_3D) {
-        double z0 = g.z_min, z1 = g.z_min + (double)g.n_slabs * g.h;
-        if (R.dz == 0.0) {
-            if (!(R.S[2] > z0 && R.S[2] < z1)) return;
-        } else {
-            double l0 = (z0 - R.S[2]) / R.dz, l1 = (z1 - R.S[2]) / R.dz;
-            if (l0 > l1) {
-                double tmp = l0;
-                l0 = l1;
-                l1 = tmp;
-            }
-            if (l0 > lo) lo = l0;
-            if (l1 < hi) hi = l1;
-        }
-    }
-    if (!(hi > lo)) return;
-    R.lo = lo;
-    R.hi = hi;
-    R.sigma = ax * R.dy - ay * R.dx;
-    // deepest ring: m0 = smallest m >= 1 with m r > d
-    int m0 = (int)floor(R.d / g.r) + 1;
-    if (m0 < 1) m0 = 1;
-    while (m0 > 1 && (double)(m0 - 1) * g.r > R.d) m0--;
-    while (m0 <= N && !((double)m0 * g.r > R.d)) m0++;
-    // rings N-1 .. m0 are crossed twice
-    double kout = kR;
-    for (int i = N - 1; i >= m0; i--) {
-        double kin = root_k((double)i, g.r, R.d, R.a);
-        double a1 = R.t - kout, b1 = R.t - kin;
-        double a2 = R.t + kin, b2 = R.t + kout;
-        walk_segment(g, rt, bdir, R, i, a1 > lo ? a1 : lo, b1 < hi ? b1 : hi, sink, status);
-        walk_segment(g, rt, bdir, R, i, a2 > lo ? a2 : lo, b2 < hi ? b2 : hi, sink, status);
-        kout = kin;
-    }
-    int i0 = m0 - 1;
-    double a0 = R.t - kout, b0 = R.t + kout;
-    walk_segment(g, rt, bdir, R, i0, a0 > lo ? a0 : lo, b0 < hi ? b0 : hi, sink, status);
-}
-
-__global__ void k_boundaries(const RingEntry *rt, int n_rings, double2 *bdir)
+__global__ void k_boundaries(const RingEntry *rt, int n_rings, double2 *bdir, float2 *bdirf)
 {
     int i = blockIdx.x;
     if (i >= n_rings) return;
     int ng = rt[i].ng, h = rt[i].head;
     for (int j = threadIdx.x; j < ng; j += blockDim.x) {
         double a = kTwoPi * (double)j / (double)ng;
-        bdir[h + j] = make_double2(cos(a), sin(a));
+        double c = cos(a), sn = sin(a);
+        bdir[h + j] = make_double2(c, sn);
+        bdirf[h + j] = make_float2((float)c, (float)sn);
     }
 }
 
-__global__ void k_count(Geometry g, const RingEntry *rt, const double2 *bdir, const int *rep_view, int n_reps,
-                        int *counts, int *status)
+// Upper bound on each row's length from the FP32 sizing walk.
+__global__ void __launch_bounds__(128) k_size(Geometry g, const RingEntry *rt, const float2 *bdirf,
+                                              const int *rep_view, int n_reps, int *caps, int mirror_from)
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_reps * g.n_rays) return;
     int rep = (int)(gid / g.n_rays), ray = (int)(gid % g.n_rays);
+    if (mirror_from > 0 && ray / g.n_u >= mirror_from) ray = (g.n_v - 1 - ray / g.n_u) * g.n_u + ray % g.n_u;
+    caps[gid] = size_ray(g, rt, bdirf, rep_view[rep], ray);
+}
+
+// z-mirror of a cone scan about the mid-plane z = 0 (source on the plane,
+// slab stack centred on it): detector row c and row n_v-1-c see mirror-image
+// rays, whose crossings are the same and whose pieces lie in slab n_s-1-s.
+// Rows of the upper half are copied from their mirror with the slab flipped.
+__global__ void k_mirror_rows(int n_reps, int n_u, int n_v, int n_rays, int mirror_from, int n_slabs,
+                              const long long *row_ptr, int *counts, uint32_t *idx, double *w64, int *status)
+{
+    long long half = (long long)(n_v - mirror_from) * n_u;
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)n_reps * half) return;
+    int rep = (int)(gid / half);
+    int q = (int)(gid % half);
+    int c = mirror_from + q / n_u, a = q % n_u;
+    long long dst = (long long)rep * n_rays + (long long)c * n_u + a;
+    long long src = (long long)rep * n_rays + (long long)(n_v - 1 - c) * n_u + a;
+    long long sb = row_ptr[src], db = row_ptr[dst], de = row_ptr[dst + 1];
+    int n = counts[src];
+    if (db + n > de) {  // the bound is the source's, so this cannot happen
+        flag(status, kStatusBounds);
+        n = (int)(de - db);
+    }
+    for (int k = 0; k < n; k++) {
+        uint32_t pc = idx[sb + k];
+        idx[db + k] = pack_cell(n_slabs - 1 - cell_slab(pc), cell_ring(pc), cell_sector(pc));
+        w64[db + k] = w64[sb + k];
+    }
+    for (long long k = db + n; k < de; k++) {
+        idx[k] = 0;
+        w64[k] = 0.0;
+    }
+    counts[dst] = n;
+}
+
+// Exact row lengths (the FP64 walk without storing); used only when a row
+// outgrew its FP32 bound.
+template <int MAXR>
+__global__ void __launch_bounds__(128) k_count(Geometry g, const RingEntry *rt, const double2 *bdir,
+                                               const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
+                                               int *status, int mirror_from)
+{
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)n_reps * g.n_rays) return;
+    int rep = (int)(gid / g.n_rays), ray = (int)(gid % g.n_rays);
+    if (mirror_from > 0 && ray / g.n_u >= mirror_from) ray = (g.n_v - 1 - ray / g.n_u) * g.n_u + ray % g.n_u;
+    uint32_t in_cell[MAXR];
     CountSink sink;
-    walk_ray(g, rt, bdir, rep_view[rep], ray, sink, status);
+    sink.in_cell = in_cell;
+    walk_ray(g, rt, bdir, bdirf, rep_view[rep], ray, sink, status);
     counts[gid] = sink.n;
 }
 
-__global__ void k_fill(Geometry g, const RingEntry *rt, const double2 *bdir, const int *rep_view, int n_reps,
-                       const int *counts, const long long *row_ptr, uint32_t *idx, double *w64, int *status)
+// FP64 walk into the row's slots [row_ptr[i], row_ptr[i+1]); writes the
+// entry count to counts[i] and pads the rest of the row (cell 0, weight 0).
+// A row with more entries than slots raises kStatusCountMismatch.
+template <int MAXR>
+__global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, const double2 *bdir,
+                                              const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
+                                              const long long *row_ptr, uint32_t *idx, double *w64, int *status,
+                                              int mirror_from)
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_reps * g.n_rays) return;
     int rep = (int)(gid / g.n_rays), ray = (int)(gid % g.n_rays);
+    if (mirror_from > 0 && ray / g.n_u >= mirror_from) return;  // built by k_mirror_rows
     long long b = row_ptr[gid], e = row_ptr[gid + 1];
+    uint32_t in_cell[MAXR];
+    int in_pos[MAXR];
     FillSink sink;
     sink.idx = idx + b;
     sink.w = w64 + b;
-    sink.cap = counts[gid];
-    walk_ray(g, rt, bdir, rep_view[rep], ray, sink, status);
-    if (sink.n != counts[gid] || sink.overflow) atomicOr(status, kStatusCountMismatch);
-    for (long long q = b + sink.n; q < e; q++) {  // row padding: cell 0, weight 0
+    sink.cap = (int)(e - b);
+    sink.in_cell = in_cell;
+    sink.in_pos = in_pos;
+    walk_ray(g, rt, bdir, bdirf, rep_view[rep], ray, sink, status);
+    if (sink.overflow) flag(status, kStatusCountMismatch);
+    counts[gid] = sink.n;
+    for (long long q = b + sink.n; q < e; q++) {
         idx[q] = 0;
         w64[q] = 0.0;
     }
+}
+
+template <int MAXR>
+static void launch_walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
+                        const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
+                        const long long *row_ptr, uint32_t *idx, double *w64, int *status, int mirror_from)
+{
+    if (fill)
+        k_fill<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status,
+                                          mirror_from);
+    else
+        k_count<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, status, mirror_from);
+}
+
+static void walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
+                 const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
+                 const long long *row_ptr, uint32_t *idx, double *w64, int *status, int mirror_from = 0)
+{
+#define USPG_WALK(M) \
+    launch_walk<M>(fill, grid, s, g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status, mirror_from)
+    if (g.n_rings <= 64) USPG_WALK(64);
+    else if (g.n_rings <= 128) USPG_WALK(128);
+    else if (g.n_rings <= 256) USPG_WALK(256);
+    else if (g.n_rings <= 512) USPG_WALK(512);
+    else USPG_WALK(1024);
+#undef USPG_WALK
 }
 
 // ---- prefix sums (exclusive, int64) -------------------------------------
@@ -642,6 +369,28 @@ __global__ void k_cell_finish(long long n_slices, const long long *slice_off, co
     }
 }
 
+// stats[rep] += row lengths of that representative; stats[n_reps] = longest row
+__global__ void k_row_stats(const int *counts, long long n_rows, int n_rays, int n_reps, long long *stats)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = i < n_rows ? counts[i] : 0;
+    long long rep = i < n_rows ? i / n_rays : -1;
+    int mx = c;
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // warps whose rows all belong to one representative reduce first
+    long long rep0 = __shfl_sync(0xffffffffu, rep, 0);
+    bool uniform = __all_sync(0xffffffffu, rep == rep0) && rep0 >= 0;
+    unsigned long long *st = (unsigned long long *)stats;
+    if (uniform) {
+        int sum = c;
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&st[rep0], (unsigned long long)sum);
+    } else if (rep >= 0) {
+        atomicAdd(&st[rep], (unsigned long long)c);
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&st[n_reps], (unsigned long long)mx);
+}
+
 __global__ void k_set_off(long long *dst, const long long *rel, long long n, long long base)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -688,61 +437,87 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_slice_off, sizeof(long long) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_meta, sizeof(uint32_t) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_width, sizeof(int) * n_slices * nreps));
+        USPG_CUDA(c, cudaMalloc(&c->d_stats, sizeof(long long) * (nreps + 1)));
         c->store_moved = true;
     }
     int *d_rep_view = c->d_rep_view, *d_counts = c->d_counts;
 
     const int TB = 128;
-    k_count<<<nblk(nrows, TB), TB, 0, s>>>(g, c->d_ring, c->d_bdir, d_rep_view, nreps, d_counts, c->d_status);
-    launch_counter()++;
-    USPG_CUDA(c, cudaGetLastError());
-    USPG_CUDA(c, exclusive_scan<int>(d_counts, nrows, kRowPad, c->d_row_ptr, s));
+    // z-mirror: a cone scan whose source sits on the mid-plane of a centred
+    // slab stack traces only detector rows c < mirror_from
+    int mirror_from = 0;
+    if (g.geometry == USPG_CONE_3D && g.z_min == -0.5 * (double)g.n_slabs * g.h && g.n_v >= 2)
+        mirror_from = (g.n_v + 1) / 2;
+    // rows sized by the FP32 bound, filled by the FP64 walk; if any row
+    // outgrows its bound the exact FP64 count sizes the rows instead
     long long nnz_pad = 0;
-    USPG_CUDA(c, cudaMemcpyAsync(&nnz_pad, c->d_row_ptr + nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    USPG_CUDA(c, cudaStreamSynchronize(s));
-
-    size_t need = (size_t)nnz_pad + kRowPad;
-    if (need > c->cap_idx) {
-        cudaFree(c->d_idx);
-        cudaFree(c->d_w);
-        cudaFree(c->d_w64);
-        c->d_idx = nullptr;
-        c->d_w = nullptr;
-        c->d_w64 = nullptr;
-        USPG_CUDA(c, cudaMalloc(&c->d_idx, sizeof(uint32_t) * need));
-        USPG_CUDA(c, cudaMalloc(&c->d_w, sizeof(WT) * need));
-        USPG_CUDA(c, cudaMalloc(&c->d_w64, sizeof(double) * need));
-        c->cap_idx = need;
-        c->store_moved = true;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        if (attempt == 0) {
+            k_size<<<nblk(nrows, TB), TB, 0, s>>>(g, c->d_ring, c->d_bdirf, d_rep_view, nreps, d_counts,
+                                                  mirror_from);
+        } else {
+            walk(false, nblk(nrows, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, nreps, d_counts,
+                 nullptr, nullptr, nullptr, c->d_status, mirror_from);
+        }
+        launch_counter()++;
+        USPG_CUDA(c, cudaGetLastError());
+        USPG_CUDA(c, exclusive_scan<int>(d_counts, nrows, kRowPad, c->d_row_ptr, s));
+        USPG_CUDA(c, cudaMemcpyAsync(&nnz_pad, c->d_row_ptr + nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        USPG_CUDA(c, cudaStreamSynchronize(s));
+        size_t need = (size_t)nnz_pad + kRowPad;
+        if (need > c->cap_idx) {
+            cudaFree(c->d_idx);
+            cudaFree(c->d_w);
+            cudaFree(c->d_w64);
+            c->d_idx = nullptr;
+            c->d_w = nullptr;
+            c->d_w64 = nullptr;
+            USPG_CUDA(c, cudaMalloc(&c->d_idx, sizeof(uint32_t) * need));
+            USPG_CUDA(c, cudaMalloc(&c->d_w, sizeof(WT) * need));
+            USPG_CUDA(c, cudaMalloc(&c->d_w64, sizeof(double) * need));
+            c->cap_idx = need;
+            c->store_moved = true;
+        }
+        walk(true, nblk(nrows, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, nreps, d_counts,
+             c->d_row_ptr, c->d_idx, c->d_w64, c->d_status, mirror_from);
+        launch_counter()++;
+        USPG_CUDA(c, cudaGetLastError());
+        if (mirror_from > 0) {
+            long long nm = (long long)nreps * (g.n_v - mirror_from) * g.n_u;
+            k_mirror_rows<<<nblk(nm, 256), 256, 0, s>>>(nreps, g.n_u, g.n_v, g.n_rays, mirror_from, g.n_slabs,
+                                                        c->d_row_ptr, d_counts, c->d_idx, c->d_w64, c->d_status);
+            launch_counter()++;
+            USPG_CUDA(c, cudaGetLastError());
+        }
+        int st = 0;
+        USPG_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        USPG_CUDA(c, cudaStreamSynchronize(s));
+        if (!(st & kStatusCountMismatch)) break;
+        if (attempt == 1) return fail(c, USPG_EDEVICE, "generator rows changed between passes");
+        USPG_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+        c->gen_fallbacks++;
     }
     double *d_w64 = c->d_w64;
-    k_fill<<<nblk(nrows, TB), TB, 0, s>>>(g, c->d_ring, c->d_bdir, d_rep_view, nreps, d_counts, c->d_row_ptr,
-                                          c->d_idx, d_w64, c->d_status);
-    launch_counter()++;
-    USPG_CUDA(c, cudaGetLastError());
     k_convert<WT><<<nblk(nrows, 256), 256, 0, s>>>(nrows, c->d_row_ptr, d_counts, d_w64,
                                                    c->weight_mode == USPG_BINARY, 1.0 / c->w_scale, (WT *)c->d_w,
                                                    c->d_rowmax);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
 
-    // statistics
-    std::vector<int> h_counts(nrows);
-    USPG_CUDA(c, cudaMemcpyAsync(h_counts.data(), d_counts, sizeof(int) * nrows, cudaMemcpyDeviceToHost, s));
-    c->h_row_ptr.resize(nrows + 1);
-    USPG_CUDA(c, cudaMemcpyAsync(c->h_row_ptr.data(), c->d_row_ptr, sizeof(long long) * (nrows + 1),
-                                 cudaMemcpyDeviceToHost, s));
+    // statistics on the device: per-representative nonzeros and longest row
+    USPG_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(long long) * (nreps + 1), s));
+    k_row_stats<<<nblk(nrows, 256), 256, 0, s>>>(d_counts, nrows, c->n_rays, nreps, c->d_stats);
+    launch_counter()++;
+    std::vector<long long> rep_nnz(nreps + 1);
+    USPG_CUDA(c, cudaMemcpyAsync(rep_nnz.data(), c->d_stats, sizeof(long long) * (nreps + 1), cudaMemcpyDeviceToHost,
+                                 s));
     USPG_CUDA(c, cudaStreamSynchronize(s));
-    long long nnz = 0, maxrow = 0;
-    std::vector<long long> rep_nnz(nreps, 0);
-    for (long long q = 0; q < nrows; q++) {
-        nnz += h_counts[q];
-        rep_nnz[q / c->n_rays] += h_counts[q];
-        maxrow = std::max<long long>(maxrow, h_counts[q]);
-    }
+    long long nnz = 0, maxrow = rep_nnz[nreps];
+    for (int q = 0; q < nreps; q++) nnz += rep_nnz[q];
     long long all = 0;
     for (int k = 0; k < c->scan.n_views; k++) all += rep_nnz[c->rep_of_view[k]];
     c->nnz_all_views = all;
+    c->h_row_ptr.clear();  // host copy made on demand by uspg_get_row
 
     // cell-major store, one representative at a time
     int *d_cell_cnt = c->d_cell_cnt, *d_cell_fill = c->d_cell_fill;
@@ -813,7 +588,8 @@ uspg_status build_store(uspg_ctx *c, cudaStream_t s)
 {
     if (!c->d_bdir) {
         USPG_CUDA(c, cudaMalloc(&c->d_bdir, sizeof(double2) * c->cells_per_slab));
-        k_boundaries<<<c->n_rings, 128, 0, s>>>(c->d_ring, c->n_rings, c->d_bdir);
+        USPG_CUDA(c, cudaMalloc(&c->d_bdirf, sizeof(float2) * c->cells_per_slab));
+        k_boundaries<<<c->n_rings, 128, 0, s>>>(c->d_ring, c->n_rings, c->d_bdir, c->d_bdirf);
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
     }

@@ -110,6 +110,7 @@ struct uspg_ctx {
     // device tables
     uspg::RingEntry *d_ring = nullptr;
     double2 *d_bdir = nullptr;  // boundary directions, indexed head + j
+    float2 *d_bdirf = nullptr;  // the same in FP32 (pre-tests)
     int slices_per_slab = 0;
     long long slices_per_rep = 0;
     // store
@@ -127,10 +128,11 @@ struct uspg_ctx {
     // generator scratch and capacities (buffers are reused across rebuilds so
     // that captured graphs stay valid; a reallocation clears the graph cache)
     int *d_counts = nullptr, *d_rep_view = nullptr, *d_cell_cnt = nullptr, *d_cell_fill = nullptr;
-    long long *d_rel = nullptr;
+    long long *d_rel = nullptr, *d_stats = nullptr;
     double *d_w64 = nullptr;
     size_t cap_idx = 0, cap_w = 0, cap_w64 = 0, cap_sell = 0;
     bool store_moved = false;
+    int gen_fallbacks = 0;  // builds whose FP32 row bound was exceeded
     long long nnz_all_views = 0;
     std::vector<long long> h_row_ptr;  // host copy for get_row
     // state

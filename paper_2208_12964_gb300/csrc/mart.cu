@@ -100,13 +100,37 @@ __global__ void __launch_bounds__(256) k_forward(const long long *__restrict__ r
     if (ray >= n_rays) return;
     long long b = row_ptr[ray], e = row_ptr[ray + 1];
     float acc = 0.0f;
-    for (long long q = b + 4 * lane; q < e; q += 128) {
-        uint4 ix = __ldg((const uint4 *)(idx + q));
-        float4 wv = load_w4(w, q);
-        acc = fmaf(wv.x, __ldg(f + rot_cell(tab, cps, ix.x)), acc);
-        acc = fmaf(wv.y, __ldg(f + rot_cell(tab, cps, ix.y)), acc);
-        acc = fmaf(wv.z, __ldg(f + rot_cell(tab, cps, ix.z)), acc);
-        acc = fmaf(wv.w, __ldg(f + rot_cell(tab, cps, ix.w)), acc);
+    // two 128-entry chunks per pass: all stream loads are issued before the
+    // eight dependent image gathers, so a typical row costs one round trip
+    // for the row and one for the gathers
+    for (long long q0 = b + 4 * lane; q0 < e; q0 += 256) {
+        long long q1 = q0 + 128;
+        bool two = q1 < e;
+        uint4 i0 = __ldg((const uint4 *)(idx + q0));
+        float4 w0 = load_w4(w, q0);
+        uint4 i1 = make_uint4(0, 0, 0, 0);
+        float4 w1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (two) {
+            i1 = __ldg((const uint4 *)(idx + q1));
+            w1 = load_w4(w, q1);
+        }
+        float g0 = __ldg(f + rot_cell(tab, cps, i0.x)), g1 = __ldg(f + rot_cell(tab, cps, i0.y));
+        float g2 = __ldg(f + rot_cell(tab, cps, i0.z)), g3 = __ldg(f + rot_cell(tab, cps, i0.w));
+        float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f;
+        if (two) {
+            h0 = __ldg(f + rot_cell(tab, cps, i1.x));
+            h1 = __ldg(f + rot_cell(tab, cps, i1.y));
+            h2 = __ldg(f + rot_cell(tab, cps, i1.z));
+            h3 = __ldg(f + rot_cell(tab, cps, i1.w));
+        }
+        acc = fmaf(w0.x, g0, acc);
+        acc = fmaf(w0.y, g1, acc);
+        acc = fmaf(w0.z, g2, acc);
+        acc = fmaf(w0.w, g3, acc);
+        acc = fmaf(w1.x, h0, acc);
+        acc = fmaf(w1.y, h1, acc);
+        acc = fmaf(w1.z, h2, acc);
+        acc = fmaf(w1.w, h3, acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -142,28 +166,40 @@ __global__ void __launch_bounds__(256) k_backward(const long long *__restrict__ 
     uint32_t meta = slice_meta[sl];
     int width = slice_width[sl];
     long long off = slice_off[sl] + lane;
-    float num = 0.0f, den = 0.0f;
-    bool zero = false;
-    for (int t = 0; t < width; t++) {
-        long long pos = off + (long long)t * kSlice;
-        uint32_t ray = __ldg(sray + pos);
-        float wv = load_w1(sw, pos);
-        float r = __ldg(res + ray);
-        bool act = (wv > 0.0f) && (r == r);
-        bool zr = act && (r == -INFINITY);
-        den += act ? wv : 0.0f;
-        zero |= zr;
-        num += (act && !zr) ? wv * r : 0.0f;
-    }
     int ring = cell_ring(meta);
     RingEntry re = rt[ring];
     int sec = cell_sector(meta) + lane;
-    if (sec < re.ng && den > 0.0f) {
-        int s2 = sec + mG * re.step;
-        s2 = s2 >= re.ng ? s2 - re.ng : s2;
-        long long cell = (long long)cell_slab(meta) * cps + re.head + s2;
-        f[cell] = zero ? 0.0f : f[cell] * expf(lambda * (num / den));
+    bool own = sec < re.ng;
+    int s2 = sec + mG * re.step;
+    s2 = s2 >= re.ng ? s2 - re.ng : s2;
+    long long cell = (long long)cell_slab(meta) * cps + re.head + s2;
+    float fv = own ? f[cell] : 0.0f;  // issued early, used at the end
+    float num = 0.0f, den = 0.0f;
+    bool zero = false;
+    // four entries per pass: stream loads first, then the ray gathers
+    for (int t = 0; t < width; t += 4) {
+        uint32_t ry[4];
+        float wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            long long pos = off + (long long)(t + u) * kSlice;
+            bool in = t + u < width;
+            ry[u] = in ? __ldg(sray + pos) : 0u;
+            wv[u] = in ? load_w1(sw, pos) : 0.0f;
+        }
+        float r[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) r[u] = __ldg(res + ry[u]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            bool act = (wv[u] > 0.0f) && (r[u] == r[u]);
+            bool zr = act && (r[u] == -INFINITY);
+            den += act ? wv[u] : 0.0f;
+            zero |= zr;
+            num += (act && !zr) ? wv[u] * r[u] : 0.0f;
+        }
     }
+    if (own && den > 0.0f) f[cell] = zero ? 0.0f : fv * expf(lambda * (num / den));
 }
 
 template <typename WT>

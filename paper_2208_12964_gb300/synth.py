@@ -19,6 +19,7 @@ Scan conventions (the same ones the library and the oracle state):
 from __future__ import annotations
 
 import math
+import re
 
 import numpy as np
 
@@ -72,6 +73,10 @@ def workload(name: str) -> dict:
         return cone_workload(128, 128, 90, 256, iterations=5, lam=0.1, seed=2, name=name)
     if name == "3d-cone-256r-256s-180v-512":
         return cone_workload(256, 256, 180, 512, iterations=5, lam=0.1, seed=3, name=name)
+    m = re.fullmatch(r"3d-cone-(\d+)r-(\d+)s-(\d+)v-(\d+)", name)
+    if m:  # same cone geometry at other sizes (profiling and test cases)
+        R, S, V, D = map(int, m.groups())
+        return cone_workload(R, S, V, D, iterations=5, lam=0.1, seed=2, name=name)
     raise KeyError(name)
 
 
