@@ -115,7 +115,7 @@ typedef struct {
     int32_t iterations;
     int32_t schedule;    /* USPG_SEQUENTIAL | USPG_PER_VIEW */
     int32_t update_rule; /* USPG_POWER | USPG_LINEAR_EQ18 (sequential only) */
-    int32_t reserved;
+    int32_t view_steps;  /* PER_VIEW: stop after this many view steps (0 = all) */
     double lambda;             /* relaxation (beta of Eq. 18), in (0, 2) */
     double stop_tol;           /* Eq. 19 tolerance; 0 = run all iterations */
     const int32_t *view_order; /* host, [n_views] permutation for PER_VIEW; NULL = 0..n_views-1 */
@@ -211,6 +211,13 @@ uspg_status uspg_resample_cartesian(uspg_ctx *ctx, int32_t mode, int32_t nx, int
 /* Kernels launched by this library in this process (graph replays count each
  * kernel node). */
 int64_t uspg_kernel_launches(void);
+/* Picks the launch shape of the per-view kernels (resident blocks per SM of
+ * the forward and of the correction kernel) by timing the candidates on view
+ * 0 of this context's own store; the image is saved and restored, so the
+ * reconstruction state does not change.  Needs coefficients and projections.
+ * choice (optional, host int32[2]) receives {forward blocks per SM,
+ * correction blocks per SM}.  Synchronous. */
+uspg_status uspg_autotune(uspg_ctx *ctx, int32_t *choice, uspg_stream stream);
 /* Runs PER_VIEW MART exactly as uspg_mart does, but launches its kernels one
  * by one with a CUDA event between consecutive launches on `stream`, and
  * returns each launch's device time: ms_forward[i], ms_backward[i] for the

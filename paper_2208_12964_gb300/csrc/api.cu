@@ -54,6 +54,16 @@ static void free_store(uspg_ctx *c)
     cudaFree(c->d_cell_fill);
     cudaFree(c->d_rel);
     cudaFree(c->d_stats);
+    cudaFree(c->d_cm_ray);
+    cudaFree(c->d_cm_w);
+    cudaFree(c->d_lane_desc);
+    c->d_cm_ray = nullptr;
+    c->d_cm_w = nullptr;
+    c->d_lane_desc = nullptr;
+    c->cap_cm = 0;
+    cudaFree(c->d_grp_ray);
+    c->d_grp_ray = nullptr;
+    c->cap_grp = 0;
     cudaFree(c->d_w64);
     c->d_counts = c->d_rep_view = c->d_cell_cnt = c->d_cell_fill = nullptr;
     c->d_rel = nullptr;
@@ -97,6 +107,8 @@ static uspg_status ensure_state(uspg_ctx *c)
     USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * c->n_cells));
     USPG_CUDA(c, cudaMalloc(&c->d_proj, sizeof(float) * (long long)c->scan.n_views * c->n_rays));
     USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * c->n_rays));
+    USPG_CUDA(c, cudaMalloc(&c->d_sacc, sizeof(float) * c->n_rays));
+    USPG_CUDA(c, cudaMemset(c->d_sacc, 0, sizeof(float) * c->n_rays));
     USPG_CUDA(c, cudaMalloc(&c->d_status, sizeof(int)));
     USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
     USPG_CUDA(c, cudaMalloc(&c->d_sweeps, sizeof(int)));
@@ -245,6 +257,7 @@ void uspg_destroy(uspg_ctx *c)
     cudaFree(c->d_f);
     cudaFree(c->d_proj);
     cudaFree(c->d_res);
+    cudaFree(c->d_sacc);
     cudaFree(c->d_status);
     cudaFree(c->d_sweeps);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -442,8 +455,10 @@ static uspg_status per_view(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s
     } else {
         std::iota(order.begin(), order.end(), 0);
     }
+    long long steps = (long long)o->iterations * nv;
+    if (o->view_steps > 0 && o->view_steps < steps) steps = o->view_steps;
     std::ostringstream key;
-    key << o->iterations << ':' << o->lambda;
+    key << steps << ':' << o->lambda;
     for (int k : order) key << ',' << k;
     auto it = c->graphs.find(key.str());
     if (it == c->graphs.end()) {
@@ -452,11 +467,11 @@ static uspg_status per_view(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s
         int64_t before = launch_counter();
         USPG_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         uspg_status st = USPG_OK;
-        for (int itn = 0; itn < o->iterations && !st; itn++)
-            for (int q = 0; q < nv && !st; q++) {
-                st = launch_forward_view(c, order[q], nullptr, c->d_res, cs);
-                if (!st) st = launch_backward_view(c, order[q], (float)o->lambda, cs);
-            }
+        for (long long q = 0; q < steps && !st; q++) {
+            int k = order[q % nv];
+            st = launch_forward_view(c, k, nullptr, c->d_res, cs);
+            if (!st) st = launch_backward_view(c, k, (float)o->lambda, cs);
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
         if (st) {
@@ -480,7 +495,7 @@ uspg_status uspg_mart(uspg_ctx *c, const uspg_mart_opts *o, uspg_stream stream)
     if (!c || !o) return fail(c, USPG_EINVAL, "NULL argument");
     if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
     if (!c->have_proj) return fail(c, USPG_ENOTREADY, "projections not set");
-    if (o->iterations < 0) return fail(c, USPG_EINVAL, "iterations must be >= 0");
+    if (o->iterations < 0 || o->view_steps < 0) return fail(c, USPG_EINVAL, "iterations and view_steps must be >= 0");
     if (!(o->lambda > 0.0) || !(o->lambda < 2.0)) return fail(c, USPG_EINVAL, "lambda must be in (0, 2)");
     cudaStream_t s = (cudaStream_t)stream;
     c->last_sweeps = o->iterations;
@@ -533,6 +548,75 @@ uspg_status uspg_mart_kernel_times(uspg_ctx *c, const uspg_mart_opts *o, float *
     if (st) return st;
     USPG_CUDA(c, e);
     *n = (int32_t)steps;
+    return USPG_OK;
+}
+
+uspg_status uspg_autotune(uspg_ctx *c, int32_t *choice, uspg_stream stream)
+{
+    if (!c) return fail(c, USPG_EINVAL, "NULL context");
+    if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    if (!c->have_proj) return fail(c, USPG_ENOTREADY, "projections not set");
+    cudaStream_t s = (cudaStream_t)stream;
+    float *saved = nullptr;
+    USPG_CUDA(c, cudaMallocAsync(&saved, sizeof(float) * c->n_cells, s));
+    USPG_CUDA(c, cudaMemcpyAsync(saved, c->d_f, sizeof(float) * c->n_cells, cudaMemcpyDeviceToDevice, s));
+    cudaEvent_t e0, e1;
+    USPG_CUDA(c, cudaEventCreate(&e0));
+    USPG_CUDA(c, cudaEventCreate(&e1));
+    // median-free best-of-4 (first run warms up) of one view's kernel
+    auto time_it = [&](bool fwd) -> float {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; rep++) {
+            cudaEventRecord(e0, s);
+            uspg_status st = fwd ? launch_forward_view(c, 0, nullptr, c->d_res, s)
+                                 : launch_backward_view(c, 0, 1e-3f, s);
+            cudaEventRecord(e1, s);
+            if (st != USPG_OK || cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;
+        }
+        return best;
+    };
+    const int fwd_opts[4] = {2, 4, 6, 8};  // resident blocks per SM of the forward
+    const int bwd_opts[4] = {2, 4, 6, 8};  // resident blocks per SM of the correction
+    float bf = 1e30f, bb = 1e30f;
+    int fb = c->fwd_blocks_per_sm, bs = c->bwd_blocks_per_sm;
+    for (int v : fwd_opts) {
+        c->fwd_blocks_per_sm = v;
+        float t = time_it(true);
+        if (t < bf) {
+            bf = t;
+            fb = v;
+        }
+    }
+    c->fwd_blocks_per_sm = fb;
+    launch_forward_view(c, 0, nullptr, c->d_res, s);
+    for (int v : bwd_opts) {
+        c->bwd_blocks_per_sm = v;
+        float t = time_it(false);
+        if (t < bb) {
+            bb = t;
+            bs = v;
+        }
+    }
+    c->bwd_blocks_per_sm = bs;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    c->err.clear();
+    USPG_CUDA(c, cudaMemcpyAsync(c->d_f, saved, sizeof(float) * c->n_cells, cudaMemcpyDeviceToDevice, s));
+    USPG_CUDA(c, cudaFreeAsync(saved, s));
+    USPG_CUDA(c, cudaStreamSynchronize(s));
+    for (auto &kv : c->graphs) {  // captured launches carry the old configuration
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    c->graphs.clear();
+    if (choice) {
+        choice[0] = fb;
+        choice[1] = bs;
+    }
     return USPG_OK;
 }
 

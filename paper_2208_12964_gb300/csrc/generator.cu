@@ -96,8 +96,10 @@ __global__ void __launch_bounds__(128) k_count(Geometry g, const RingEntry *rt, 
     int rep = (int)(gid / g.n_rays), ray = (int)(gid % g.n_rays);
     if (mirror_from > 0 && ray / g.n_u >= mirror_from) ray = (g.n_v - 1 - ray / g.n_u) * g.n_u + ray % g.n_u;
     uint32_t in_cell[MAXR];
+    double root[MAXR];
     CountSink sink;
     sink.in_cell = in_cell;
+    sink.root = root;
     walk_ray(g, rt, bdir, bdirf, rep_view[rep], ray, sink, status);
     counts[gid] = sink.n;
 }
@@ -118,7 +120,9 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
     long long b = row_ptr[gid], e = row_ptr[gid + 1];
     uint32_t in_cell[MAXR];
     int in_pos[MAXR];
+    double root[MAXR];
     FillSink sink;
+    sink.root = root;
     sink.idx = idx + b;
     sink.w = w64 + b;
     sink.cap = (int)(e - b);
@@ -397,6 +401,52 @@ __global__ void k_set_off(long long *dst, const long long *rel, long long n, lon
     if (i < n) dst[i] = base + rel[i] * kSlice;
 }
 
+// ---- cell-major store with lanes ordered by ray count ----------------------------
+//
+// In each 32-cell slice the lanes are permuted so that ray counts fall from
+// lane 0 to lane 31; row t of the slice then holds its present entries in a
+// prefix of its 32 slots, and a kernel lane l reads entry t of its cell at
+// slice_off + 32 t + l whenever t < count(l) -- addresses that depend on no
+// loaded data, with the absent slots never fetched.  lane_desc[32 s + l] =
+// (source lane << 11) | count.
+
+template <typename WT>
+__global__ void k_sort_lanes(long long n_slices, const uint32_t *meta, const int *width, const long long *slice_off,
+                             const RingEntry *rt, long long cps, const int *cell_cnt, const uint32_t *sray,
+                             const WT *sw, uint16_t *lane_desc, uint32_t *dray, WT *dw)
+{
+    long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (sl >= n_slices) return;
+    uint32_t m = meta[sl];
+    int ring = cell_ring(m), sec = cell_sector(m) + lane;
+    int cnt = sec < rt[ring].ng ? cell_cnt[(long long)cell_slab(m) * cps + rt[ring].head + sec] : 0;
+    int rank = 0;  // position of this lane in descending count order (ties by lane)
+    for (int o = 0; o < 32; o++) {
+        int co = __shfl_sync(0xffffffffu, cnt, o);
+        rank += (co > cnt) || (co == cnt && o < lane);
+    }
+    lane_desc[sl * 32 + rank] = (uint16_t)((lane << 11) | cnt);
+    long long off = slice_off[sl];
+    int W = width[sl];
+    for (int t = 0; t < W; t++) {
+        if (t < cnt) {
+            dray[off + (long long)t * kSlice + rank] = sray[off + (long long)t * kSlice + lane];
+            dw[off + (long long)t * kSlice + rank] = sw[off + (long long)t * kSlice + lane];
+        }
+    }
+}
+
+// ray of every aligned group of kRowPad entries of the ray-major store (rows
+// start and end on group boundaries, so a group never straddles two rays)
+__global__ void k_group_rays(const long long *row_ptr, long long n_rows, int n_rays, uint32_t *grp_ray)
+{
+    long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_rows) return;
+    uint32_t ray = (uint32_t)(row % n_rays);
+    for (long long g = row_ptr[row] / kRowPad; g < row_ptr[row + 1] / kRowPad; g++) grp_ray[g] = ray;
+}
+
 static unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <typename WT>
@@ -518,13 +568,19 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     for (int k = 0; k < c->scan.n_views; k++) all += rep_nnz[c->rep_of_view[k]];
     c->nnz_all_views = all;
     c->h_row_ptr.clear();  // host copy made on demand by uspg_get_row
+    c->h_rep_entry0.assign(nreps + 1, 0);
+    for (int q = 0; q <= nreps; q++)
+        USPG_CUDA(c, cudaMemcpyAsync(&c->h_rep_entry0[q], c->d_row_ptr + (long long)q * c->n_rays, sizeof(long long),
+                                     cudaMemcpyDeviceToHost, s));
 
     // cell-major store, one representative at a time
     int *d_cell_cnt = c->d_cell_cnt, *d_cell_fill = c->d_cell_fill;
     long long *d_rel = c->d_rel;
-    // pass 1: slice widths and absolute offsets
+    // pass 1: slice widths and offsets
     long long sell = 0;
+    c->h_sell_base.assign(nreps + 1, 0);
     for (int rep = 0; rep < nreps; rep++) {
+        c->h_sell_base[rep] = sell;
         const long long *rp = c->d_row_ptr + (long long)rep * c->n_rays;
         const int *cn = d_counts + (long long)rep * c->n_rays;
         USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
@@ -543,7 +599,9 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMemcpyAsync(&tot, d_rel + n_slices, sizeof(long long), cudaMemcpyDeviceToHost, s));
         USPG_CUDA(c, cudaStreamSynchronize(s));
         sell += tot * kSlice;
+        if (tot * kSlice >= (1LL << 32)) return fail(c, USPG_EUNSUPPORTED, "a view's cell-major store exceeds 2^32 slots");
     }
+    c->h_sell_base[nreps] = sell;
     if ((size_t)(sell + kSlice) > c->cap_sell) {
         cudaFree(c->d_sray);
         cudaFree(c->d_sw);
@@ -552,6 +610,24 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_sray, sizeof(uint32_t) * (sell + kSlice)));
         USPG_CUDA(c, cudaMalloc(&c->d_sw, sizeof(WT) * (sell + kSlice)));
         c->cap_sell = sell + kSlice;
+        c->store_moved = true;
+    }
+    if ((size_t)(sell + kSlice) > c->cap_cm) {  // lane-ordered copy of the padded layout
+        cudaFree(c->d_cm_ray);
+        cudaFree(c->d_cm_w);
+        cudaFree(c->d_lane_desc);
+        c->d_cm_ray = nullptr;
+        c->d_cm_w = nullptr;
+        c->d_lane_desc = nullptr;
+        USPG_CUDA(c, cudaMalloc(&c->d_cm_ray, sizeof(uint32_t) * (sell + kSlice)));
+        USPG_CUDA(c, cudaMalloc(&c->d_cm_w, sizeof(WT) * (sell + kSlice)));
+        USPG_CUDA(c, cudaMemsetAsync(c->d_cm_ray, 0, sizeof(uint32_t) * (sell + kSlice), s));
+        USPG_CUDA(c, cudaMemsetAsync(c->d_cm_w, 0, sizeof(WT) * (sell + kSlice), s));
+        c->cap_cm = sell + kSlice;
+        c->store_moved = true;
+    }
+    if (!c->d_lane_desc) {
+        USPG_CUDA(c, cudaMalloc(&c->d_lane_desc, sizeof(uint16_t) * 32 * n_slices * nreps));
         c->store_moved = true;
     }
     // pass 2: scatter each row entry to its cell's column, then sort and pad
@@ -573,9 +649,25 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                                                                    c->cells_per_slab, d_cell_cnt, c->d_sray,
                                                                    (WT *)c->d_sw);
         launch_counter()++;
+        k_sort_lanes<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(
+            n_slices, c->d_slice_meta + rep * n_slices, c->d_slice_width + rep * n_slices, so, c->d_ring,
+            c->cells_per_slab, d_cell_cnt, c->d_sray, (const WT *)c->d_sw, c->d_lane_desc + 32 * rep * n_slices,
+            c->d_cm_ray, (WT *)c->d_cm_w);
+        launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
     }
+    if (nnz_pad / kRowPad + 1 > c->cap_grp) {
+        cudaFree(c->d_grp_ray);
+        c->d_grp_ray = nullptr;
+        USPG_CUDA(c, cudaMalloc(&c->d_grp_ray, sizeof(uint32_t) * (nnz_pad / kRowPad + 1)));
+        c->cap_grp = nnz_pad / kRowPad + 1;
+        c->store_moved = true;
+    }
+    k_group_rays<<<nblk(nrows, 256), 256, 0, s>>>(c->d_row_ptr, nrows, c->n_rays, c->d_grp_ray);
+    launch_counter()++;
+
     USPG_CUDA(c, cudaStreamSynchronize(s));
+
     c->gen.n_reps = nreps;
     c->gen.nnz = nnz;
     c->gen.nnz_pad = nnz_pad;

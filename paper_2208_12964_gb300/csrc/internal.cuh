@@ -21,9 +21,10 @@ constexpr double kMinPiece = 1e-9;            // fraction of a cell dropped as a
 constexpr int kMaxRings = 1024;
 constexpr int kMaxSlabs = 1024;
 constexpr int kMaxSectors = 4096;
-constexpr int kRowPad = 4;       // ray-major rows are padded to a multiple of this
+constexpr int kRowPad = 8;       // ray-major rows are padded to a multiple of this (16 B of FP16)
 constexpr int kSlice = 32;       // cells per slice of the cell-major store
 constexpr int kMaxRing0Cross = 32;
+constexpr int kTileAlign = 8;  // tiles start on a multiple of this many entries
 
 // device status bits (uspg_sync)
 constexpr int kStatusCountMismatch = 1;
@@ -124,6 +125,16 @@ struct uspg_ctx {
     int *d_slice_width = nullptr;
     uint32_t *d_sray = nullptr;
     void *d_sw = nullptr;
+    // cell-major store with the lanes of every slice ordered by ray count
+    uint32_t *d_cm_ray = nullptr;    // [slots] ray ids
+    void *d_cm_w = nullptr;          // [slots] weights, stored dtype
+    uint16_t *d_lane_desc = nullptr; // [reps][slices][32] (source lane << 11) | count
+    long long cap_cm = 0;
+    uint32_t *d_grp_ray = nullptr;      // ray of each kRowPad-entry group of the ray-major store
+    long long cap_grp = 0;
+    float *d_sacc = nullptr;            // per-ray sum accumulator of the forward (kept zero between views)
+    // launch shape of the per-view kernels (autotuned): resident blocks per SM
+    int fwd_blocks_per_sm = 0, bwd_blocks_per_sm = 0;
     uspg::GenOut gen{};
     // generator scratch and capacities (buffers are reused across rebuilds so
     // that captured graphs stay valid; a reallocation clears the graph cache)
@@ -135,6 +146,8 @@ struct uspg_ctx {
     int gen_fallbacks = 0;  // builds whose FP32 row bound was exceeded
     long long nnz_all_views = 0;
     std::vector<long long> h_row_ptr;  // host copy for get_row
+    std::vector<long long> h_rep_entry0;  // first ray-major entry of each representative (+ end)
+    std::vector<long long> h_sell_base;   // first cell-major slot of each representative
     // state
     float *d_f = nullptr;
     float *d_proj = nullptr;

@@ -22,6 +22,7 @@
 // registers while the current ray is reduced and corrected.
 #include "internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace uspg {
@@ -202,18 +203,276 @@ __global__ void __launch_bounds__(256) k_backward(const long long *__restrict__ 
     if (own && den > 0.0f) f[cell] = zero ? 0.0f : fv * expf(lambda * (num / den));
 }
 
+// ---- per-view forward: entry-parallel ------------------------------------------
+//
+// Rows of the ray-major store start and end on multiples of kRowPad (= 8)
+// entries, so every aligned group of 8 entries belongs to one ray (grp_ray).
+// Each lane takes one group: two 16-byte index loads, the weights, eight
+// independent image gathers; lanes holding the same ray (consecutive) are
+// combined by a segmented shuffle reduction and the first lane of each ray
+// segment adds the partial sum into sacc[ray].  The coefficient stream is
+// read with evict-first loads (__ldcs) so the image stays in L2 across views.
+// k_forward_finalize turns the sums into ln(P/Pbar) and clears sacc.
+
+__device__ __forceinline__ void load_w8(const float *w, long long q, float o[8])
+{
+    float4 a = __ldcs((const float4 *)(w + q)), b = __ldcs((const float4 *)(w + q + 4));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void load_w8(const __half *w, long long q, float o[8])
+{
+    uint4 u = __ldcs((const uint4 *)(w + q));
+    const __half2 *h = (const __half2 *)&u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float2 v = __half22float2(h[i]);
+        o[2 * i] = v.x;
+        o[2 * i + 1] = v.y;
+    }
+}
+__device__ __forceinline__ void load_w8(const __nv_bfloat16 *w, long long q, float o[8])
+{
+    uint4 u = __ldcs((const uint4 *)(w + q));
+    const __nv_bfloat162 *h = (const __nv_bfloat162 *)&u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float2 v = __bfloat1622float2(h[i]);
+        o[2 * i] = v.x;
+        o[2 * i + 1] = v.y;
+    }
+}
+__device__ __forceinline__ float load_cs(const float *w, long long q) { return __ldcs(w + q); }
+__device__ __forceinline__ float load_cs(const __half *w, long long q)
+{
+    return __half2float(__ushort_as_half(__ldcs((const unsigned short *)(w + q))));
+}
+__device__ __forceinline__ float load_cs(const __nv_bfloat16 *w, long long q)
+{
+    return __bfloat162float(__ushort_as_bfloat16(__ldcs((const unsigned short *)(w + q))));
+}
+
+template <typename WT>
+struct Group8 {
+    uint32_t c[8];
+    float w[8];
+    uint32_t ray;
+};
+
+template <typename WT>
+__device__ __forceinline__ void load_group(Group8<WT> &G, const uint32_t *idx, const WT *w, const uint32_t *grp_ray,
+                                           long long g, bool valid)
+{
+    if (valid) {
+        long long q = g * kRowPad;
+        uint4 ia = __ldcs((const uint4 *)(idx + q)), ib = __ldcs((const uint4 *)(idx + q + 4));
+        load_w8(w, q, G.w);
+        G.ray = __ldcs(grp_ray + g);
+        G.c[0] = ia.x; G.c[1] = ia.y; G.c[2] = ia.z; G.c[3] = ia.w;
+        G.c[4] = ib.x; G.c[5] = ib.y; G.c[6] = ib.z; G.c[7] = ib.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            G.c[i] = 0;
+            G.w[i] = 0.0f;
+        }
+        G.ray = 0xffffffffu;
+    }
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict__ idx, const WT *__restrict__ w,
+                                                      const uint32_t *__restrict__ grp_ray, long long g0,
+                                                      long long n_groups, const float *__restrict__ f,
+                                                      const RingEntry *__restrict__ rt, int n_rings, int mG,
+                                                      long long cps, float *__restrict__ sacc)
+{
+    extern __shared__ int4 tab[];
+    fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long step = (((long long)gridDim.x * blockDim.x) >> 5) * 32;
+    long long base = gw * 32;
+    if (base >= n_groups) return;
+    // two register buffers: the next chunk's stream loads are in flight while
+    // the current chunk's gathers wait
+    Group8<WT> cur, nxt;
+    load_group(cur, idx, w, grp_ray, g0 + base + lane, base + lane < n_groups);
+    for (; base < n_groups; base += step) {
+        long long nb = base + step;
+        load_group(nxt, idx, w, grp_ray, g0 + nb + lane, nb + lane < n_groups);
+        float gv[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) gv[i] = cur.w[i] != 0.0f ? __ldg(f + rot_cell(tab, cps, cur.c[i])) : 0.0f;
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; i++) acc = fmaf(cur.w[i], gv[i], acc);
+        uint32_t ray = cur.ray;
+        // segmented sum over lanes of the same ray (they are consecutive)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            float v2 = __shfl_down_sync(0xffffffffu, acc, o);
+            uint32_t r2 = __shfl_down_sync(0xffffffffu, ray, o);
+            if (lane + o < 32 && r2 == ray) acc += v2;
+        }
+        uint32_t rprev = __shfl_up_sync(0xffffffffu, ray, 1);
+        if (ray != 0xffffffffu && (lane == 0 || rprev != ray)) atomicAdd(&sacc[ray], acc);
+        cur = nxt;
+    }
+}
+
+__global__ void k_forward_finalize(float *__restrict__ sacc, const float *__restrict__ proj, int n_rays, float w_scale,
+                                   float *__restrict__ out_s, float *__restrict__ out_res)
+{
+    int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= n_rays) return;
+    float sv = sacc[ray] * w_scale;
+    sacc[ray] = 0.0f;
+    if (out_s) out_s[ray] = sv;
+    if (out_res) {
+        float res;
+        if (!(sv > 0.0f)) {
+            res = __int_as_float(0x7fc00000);  // empty row or zero sum: skip this ray
+        } else {
+            float p = proj[ray];
+            res = p > 0.0f ? logf(p / sv) : -INFINITY;
+        }
+        out_res[ray] = res;
+    }
+}
+
+// ---- per-view correction: lane-ordered cell-major store --------------------------
+//
+// One warp takes SPW slices (32 cells each).  Lane l of a slice owns the cell
+// of its source lane (lane_desc) and its count n; its t-th ray is at
+// slice_off + 32 t + l for t < n.  All stream loads of the warp's slices are
+// issued before the ray-value gathers, and the image value of each cell is
+// fetched first so that its latency overlaps the stream.
+struct SliceDesc {
+    uint32_t d, m, off;
+};
+
+__device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_off, long long base,
+                                          const uint32_t *slice_meta, const uint16_t *lane_desc, long long sl,
+                                          long long n_slices, int lane)
+{
+    if (sl < n_slices) {
+        D.d = lane_desc[sl * 32 + lane];
+        D.m = slice_meta[sl];
+        D.off = (uint32_t)(slice_off[sl] - base);
+    } else {
+        D.d = 0;
+        D.m = 0;
+        D.off = 0;
+    }
+}
+
+// rows 0..R-1 of one lane: loads first, then the ray-value gathers
+template <typename WT, int R>
+__device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, const float *res, uint32_t off, int cnt,
+                                        float &num, float &den, bool &zero)
+{
+    uint32_t ry[R];
+    float wv[R], rv[R];
+#pragma unroll
+    for (int t = 0; t < R; t++) {
+        bool in = t < cnt;
+        uint32_t pos = off + (uint32_t)t * kSlice;
+        ry[t] = in ? __ldcs(cray + pos) : 0u;
+        wv[t] = in ? load_cs(cw, pos) : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg(res + ry[t]) : 0.f;
+#pragma unroll
+    for (int t = 0; t < R; t++) {
+        bool act = (wv[t] > 0.0f) && (rv[t] == rv[t]);
+        bool zr = act && (rv[t] == -INFINITY);
+        den += act ? wv[t] : 0.0f;
+        zero |= zr;
+        num += (act && !zr) ? wv[t] * rv[t] : 0.0f;
+    }
+}
+
+// Persistent warps, one slice per step: the next slice's descriptor loads are
+// issued before the current slice's gathers.  The slice's widest column is
+// lane 0's (lanes are ordered by count), so the unrolled row loop is sized
+// per slice (warp-uniform) to 2, 4 or 8 rows, with a loop beyond.
+template <typename WT>
+__global__ void __launch_bounds__(256) k_backward_sell(const long long *__restrict__ slice_off, long long base,
+                                                       const uint32_t *__restrict__ slice_meta,
+                                                       const uint16_t *__restrict__ lane_desc,
+                                                       const uint32_t *__restrict__ cray, const WT *__restrict__ cw,
+                                                       const float *__restrict__ res, float *__restrict__ f,
+                                                       const RingEntry *__restrict__ rt, int mG, long long cps,
+                                                       long long n_slices, float lambda)
+{
+    const int lane = threadIdx.x & 31;
+    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long W = ((long long)gridDim.x * blockDim.x) >> 5;
+    long long sl = wg;
+    if (sl >= n_slices) return;
+    const uint32_t *cr = cray + base;
+    const WT *cwb = cw + base;
+    SliceDesc cur, nxt;
+    load_desc(cur, slice_off, base, slice_meta, lane_desc, sl, n_slices, lane);
+    for (; sl < n_slices; sl += W) {
+        int cnt = (int)(cur.d & 2047u);
+        int width = __shfl_sync(0xffffffffu, cnt, 0);
+        RingEntry re = rt[cell_ring(cur.m)];
+        int sec = cell_sector(cur.m) + (int)(cur.d >> 11);
+        int s2 = sec + mG * re.step;
+        s2 = s2 >= re.ng ? s2 - re.ng : s2;
+        long long cell = (long long)cell_slab(cur.m) * cps + re.head + s2;
+        float fv = cnt > 0 ? f[cell] : 0.0f;
+        uint32_t off = cur.off + lane;
+        load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
+        float num = 0.f, den = 0.f;
+        bool zero = false;
+        if (width <= 2) {
+            cm_rows<WT, 2>(cr, cwb, res, off, cnt, num, den, zero);
+        } else if (width <= 4) {
+            cm_rows<WT, 4>(cr, cwb, res, off, cnt, num, den, zero);
+        } else {
+            cm_rows<WT, 8>(cr, cwb, res, off, cnt, num, den, zero);
+            for (int t = 8; t < cnt; t++) {  // long columns (cells close to the source)
+                uint32_t pos = off + (uint32_t)t * kSlice;
+                float wt = load_cs(cwb, pos);
+                float r = __ldg(res + __ldcs(cr + pos));
+                bool act = (wt > 0.0f) && (r == r);
+                bool zr = act && (r == -INFINITY);
+                den += act ? wt : 0.0f;
+                zero |= zr;
+                num += (act && !zr) ? wt * r : 0.0f;
+            }
+        }
+        if (den > 0.0f) f[cell] = zero ? 0.0f : fv * expf(lambda * (num / den));
+        cur = nxt;
+    }
+}
+
 template <typename WT>
 static uspg_status fwd_typed(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s)
 {
     int rep = c->rep_of_view[view];
     int mG = c->m_of_view[view] % c->G;
-    StoreView v = store_view(c, rep);
+    const long long *rp = c->d_row_ptr + (long long)rep * c->n_rays;
+    long long g0 = c->h_rep_entry0[rep] / kRowPad, ng = (c->h_rep_entry0[rep + 1] - c->h_rep_entry0[rep]) / kRowPad;
+    (void)rp;
     const int TB = 256;
-    unsigned grid = (unsigned)(((long long)c->n_rays * 32 + TB - 1) / TB);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = c->fwd_blocks_per_sm > 0 ? c->fwd_blocks_per_sm : 8;
+    long long want = (ng + TB - 1) / TB;  // one group per thread
+    long long grid = std::min<long long>(want, (long long)sms * per_sm);
+    if (grid < 1) grid = 1;
     size_t smem = sizeof(int4) * c->n_rings;
-    k_forward<WT><<<grid, TB, smem, s>>>(v.row_ptr, v.idx, (const WT *)v.w, c->d_f, c->d_ring, c->n_rings, mG,
-                                         c->cells_per_slab, c->d_proj + (long long)view * c->n_rays, c->n_rays,
-                                         (float)c->w_scale, out_s, out_res);
+    k_forward_flat<WT><<<(unsigned)grid, TB, smem, s>>>(c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, c->d_f,
+                                                        c->d_ring, c->n_rings, mG, c->cells_per_slab, c->d_sacc);
+    launch_counter()++;
+    USPG_CUDA(c, cudaGetLastError());
+    k_forward_finalize<<<(unsigned)((c->n_rays + 255) / 256), 256, 0, s>>>(
+        c->d_sacc, c->d_proj + (long long)view * c->n_rays, c->n_rays, (float)c->w_scale, out_s, out_res);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
     return USPG_OK;
@@ -231,11 +490,19 @@ static uspg_status bwd_typed(uspg_ctx *c, int view, float lambda, cudaStream_t s
 {
     int rep = c->rep_of_view[view];
     int mG = c->m_of_view[view] % c->G;
-    StoreView v = store_view(c, rep);
+    const long long S = c->slices_per_rep;
     const int TB = 256;
-    unsigned grid = (unsigned)((c->slices_per_rep * 32 + TB - 1) / TB);
-    k_backward<WT><<<grid, TB, 0, s>>>(v.slice_off, v.slice_meta, v.slice_width, v.sray, (const WT *)v.sw, c->d_res,
-                                       c->d_f, c->d_ring, mG, c->cells_per_slab, c->slices_per_rep, lambda);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = c->bwd_blocks_per_sm > 0 ? c->bwd_blocks_per_sm : 8;
+    long long want = (S * 32 + TB - 1) / TB;
+    long long grid = std::min<long long>(want, (long long)sms * per_sm);
+    if (grid < 1) grid = 1;
+    long long base = c->h_sell_base[rep];
+    k_backward_sell<WT><<<(unsigned)grid, TB, 0, s>>>(c->d_slice_off + rep * S, base, c->d_slice_meta + rep * S,
+                                                      c->d_lane_desc + 32 * rep * S, c->d_cm_ray, (const WT *)c->d_cm_w,
+                                                      c->d_res, c->d_f, c->d_ring, mG, c->cells_per_slab, S, lambda);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
     return USPG_OK;

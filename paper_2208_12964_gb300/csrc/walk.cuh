@@ -80,6 +80,7 @@ struct CountSink {
     uint32_t last = 0xffffffffu;
     bool outbound = false;
     uint32_t *in_cell = nullptr;
+    double *root = nullptr;  // per-ring scratch: circle roots of the inbound half
     USPG_HD void emit(uint32_t cell, double)
     {
         if (n > 0 && cell == last) return;
@@ -105,6 +106,7 @@ struct FillSink {
     bool outbound = false;
     uint32_t *in_cell = nullptr;
     int *in_pos = nullptr;
+    double *root = nullptr;
     USPG_HD void emit(uint32_t cell, double len)
     {
         if (last_pos >= 0 && cell == last) {
@@ -506,9 +508,12 @@ USPG_HD void walk_ray(const Geometry &g, const RingEntry *rt, const double2 *bdi
     // m0 .. N-1 outbound.
     for (int i = 0; i < N; i++) sink.in_cell[i] = 0xffffffffu;
     sink.outbound = false;
+    // each circle's root is formed once: the inbound half keeps it (in the
+    // sink's per-ring scratch) for the outbound half
     double kout = kR;
     for (int i = N - 1; i >= m0; i--) {
         double kin = root_k((double)i, g.r, R.d, R.a);
+        sink.root[i] = kin;
         double a1 = R.t - kout, b1 = R.t - kin;
         walk_segment(g, rt, bdir, bdirf, R, i, a1 > lo ? a1 : lo, b1 < hi ? b1 : hi, sink, status);
         kout = kin;
@@ -519,7 +524,7 @@ USPG_HD void walk_ray(const Geometry &g, const RingEntry *rt, const double2 *bdi
     sink.outbound = true;
     double kin = kout;
     for (int i = m0; i <= N - 1; i++) {
-        double ko = (i == N - 1) ? kR : root_k((double)(i + 1), g.r, R.d, R.a);
+        double ko = (i == N - 1) ? kR : sink.root[i + 1];
         double a2 = R.t + kin, b2 = R.t + ko;
         walk_segment(g, rt, bdir, bdirf, R, i, a2 > lo ? a2 : lo, b2 < hi ? b2 : hi, sink, status);
         kin = ko;

@@ -50,7 +50,7 @@ class CoeffOpts(C.Structure):
 
 class MartOpts(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("schedule", C.c_int32), ("update_rule", C.c_int32),
-                ("reserved", C.c_int32), ("lambda_", C.c_double), ("stop_tol", C.c_double),
+                ("view_steps", C.c_int32), ("lambda_", C.c_double), ("stop_tol", C.c_double),
                 ("view_order", C.c_void_p)]
 
 
@@ -87,6 +87,7 @@ def lib():
             "uspg_resample_cartesian": ([V, I32, I32, I32, V, I32, V], I32),
             "uspg_kernel_launches": ([], I64),
             "uspg_mart_kernel_times": ([V, P(MartOpts), V, V, I32, P(I32), V], I32),
+            "uspg_autotune": ([V, V, V], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -200,9 +201,9 @@ def uspg_get_image(ctx, f, to_device: bool, stream=None):
 
 
 def mart_opts(iterations: int, lam: float, schedule: int, rule: int = POWER, stop_tol: float = 0.0,
-              view_order=None):
+              view_order=None, view_steps: int = 0):
     keep = None
-    o = MartOpts(iterations=iterations, schedule=schedule, update_rule=rule, reserved=0, lambda_=lam,
+    o = MartOpts(iterations=iterations, schedule=schedule, update_rule=rule, view_steps=view_steps, lambda_=lam,
                  stop_tol=stop_tol, view_order=None)
     if view_order is not None:
         keep = np.ascontiguousarray(view_order, np.int32)
@@ -240,3 +241,11 @@ def uspg_mart_kernel_times(ctx, opts: MartOpts, steps: int, stream=None):
     _check(lib().uspg_mart_kernel_times(ctx, C.byref(opts), fw.ctypes.data, bw.ctypes.data, len(fw), C.byref(n),
                                         _stream(stream)), ctx)
     return fw[:n.value], bw[:n.value]
+
+
+def uspg_autotune(ctx, stream=None):
+    """Times the per-view kernels' launch shapes; returns the choice
+    (forward blocks per SM, correction blocks per SM)."""
+    ch = np.zeros(2, np.int32)
+    _check(lib().uspg_autotune(ctx, ch.ctypes.data, _stream(stream)), ctx)
+    return tuple(int(x) for x in ch)

@@ -165,6 +165,14 @@ def test_mart_per_view_3d_noisy(torch_cuda):
     o = oracle_for(spec)
     f0 = np.ones(o.n_cells)
     ref = o.mart_per_view(proj, f0, 3, 0.1)
+    # tuning the stage ring leaves the image untouched and the result equal
+    g.U.uspg_set_projections(g.ctx, proj, False)
+    g.U.uspg_set_image(g.ctx, np.full(o.n_cells, 0.5, np.float32), False)
+    choice = g.U.uspg_autotune(g.ctx)
+    assert choice[0] in (2, 4, 6, 8) and choice[1] in (2, 4, 6, 8)
+    kept = np.zeros(o.n_cells, np.float32)
+    g.U.uspg_get_image(g.ctx, kept, False)
+    assert np.all(kept == 0.5)
     got = _run_mart(g, proj, f0, 3, 0.1, 1)
     assert rel_l2(got, ref) < TOL_IMG
     assert np.all(got >= 0) and np.any(got == 0)  # noisy zero rays zero their cells
@@ -182,6 +190,33 @@ def test_mart_per_view_2d_custom_order(torch_cuda):
     assert rel_l2(got, ref) < TOL_IMG
 
 
+def test_mart_per_view_full_size_first_view(torch_cuda):
+    """The 128-ring, 128-slab, 90-view cone at full size, in the bench's launch
+    configuration: one per-view step (view 0, f0 = 1) against the oracle's
+    one-step image over all 6.3 M cells; then the whole first sweep's image
+    stays finite, non-negative and changes only where rays pass."""
+    spec = synth.workload("3d-cone-128r-128s-90v-256")
+    proj = synth.projections(spec)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    U = g.U
+    U.uspg_set_projections(g.ctx, proj, False)
+    U.uspg_fill_image(g.ctx, 1.0)
+    U.uspg_autotune(g.ctx)
+    opts, keep = U.mart_opts(1, 0.1, U.PER_VIEW, view_steps=1)
+    U.uspg_mart(g.ctx, opts)
+    U.uspg_sync(g.ctx)
+    got = np.zeros(o.n_cells, np.float32)
+    U.uspg_get_image(g.ctx, got, False)
+    ref = np.ones(o.n_cells)
+    o.set_threads(16)
+    o.mart_views_sample(proj, ref, [0], 0.1)
+    hit = ref != 1.0
+    assert hit.sum() > 0.5 * o.n_cells
+    assert np.all(got[~hit] == 1.0)
+    nz = ref > 0
+    assert np.all(got[~nz] == 0.0)
+    assert np.max(np.abs(got[nz] - ref[nz]) / ref[nz]) < 2e-5
 # --------------------------------------------------------------- resample ---
 
 def test_resample_point_and_bijection(torch_cuda):
