@@ -206,6 +206,37 @@ uspg_status uspg_mart_sweeps(uspg_ctx *ctx, int32_t *sweeps);
 uspg_status uspg_resample_cartesian(uspg_ctx *ctx, int32_t mode, int32_t nx, int32_t ny, float *out,
                                     int32_t out_on_device, uspg_stream stream);
 
+/* --- projection without device allocation ------------------------------------------ */
+
+/* Capacity, in rays, of the accumulator used by uspg_forward_project_noalloc. */
+#define USPG_NOALLOC_MAX_RAYS (1 << 20)
+
+/* Forward projection of one view, out = A_view f (the ray sums of Eq. 17),
+ * for callers that must not allocate device memory while they run: processes
+ * whose device memory is owned by a pooling allocator with a fixed budget
+ * (an allocation outside the pool can fail or fragment memory the pool
+ * expects to own), and latency-critical loops that forbid cudaMalloc after
+ * start-up because it can synchronise the device and take milliseconds.  The
+ * paper has no counterpart: this is an engineering entry point of the library.
+ *
+ * ctx: a context whose coefficients are built (read only).  view: 0-based.
+ * f: device float32 [cells], the image to project (the context's own image is
+ * not used).  out: device float32 [rays].  Work is enqueued on `stream`.
+ *
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Its ray-sum accumulator is a file-scope __device__ array of
+ * USPG_NOALLOC_MAX_RAYS floats (4 MiB) that every GPU which loads this
+ * library holds until the process exits.  The first call on a device looks
+ * up that array's address (cudaGetSymbolAddress, with the device current) and
+ * keeps it; make that first call on each device before any stream capture.
+ * All calls share the one array: each call clears the part it uses before
+ * accumulating, and calls whose work overlaps on the GPU (on different
+ * streams, or from different host threads) race on it and give wrong sums --
+ * serialise them.  EINVAL if the view's rays exceed USPG_NOALLOC_MAX_RAYS or
+ * a pointer is NULL; ENOTREADY without coefficients. */
+uspg_status uspg_forward_project_noalloc(const uspg_ctx *ctx, int32_t view, const float *f, float *out,
+                                         uspg_stream stream);
+
 /* --- instrumentation ------------------------------------------------------------ */
 
 /* Kernels launched by this library in this process (graph replays count each

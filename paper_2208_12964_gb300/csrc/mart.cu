@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace uspg {
 
@@ -692,4 +693,85 @@ uspg_status launch_sequential(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t
     return seq_typed<float>(c, o, s);
 }
 
+// ---- forward projection without device allocation ---------------------------------
+//
+// The ray-sum accumulator of uspg_forward_project_noalloc lives in this
+// file-scope array instead of a context allocation.  Host code must not use
+// the symbol as an address: it is resolved per device with
+// cudaGetSymbolAddress and cached.
+static __device__ __align__(256) float g_noalloc_acc[USPG_NOALLOC_MAX_RAYS];
+
+__global__ void k_clear_acc(float *acc, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) acc[i] = 0.0f;
+}
+
+constexpr int kMaxDevices = 64;
+
+// device address of g_noalloc_acc on the current device (looked up once)
+static cudaError_t noalloc_acc(float **out)
+{
+    static std::mutex mu;
+    static float *addr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_acc);
+        if (e != cudaSuccess) return e;
+        addr[dev] = (float *)p;
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+template <typename WT>
+static uspg_status fwd_noalloc_typed(uspg_ctx *c, int view, const float *f, float *out, float *acc, cudaStream_t s)
+{
+    int rep = c->rep_of_view[view];
+    int mG = c->m_of_view[view] % c->G;
+    long long g0 = c->h_rep_entry0[rep] / kRowPad, ng = (c->h_rep_entry0[rep + 1] - c->h_rep_entry0[rep]) / kRowPad;
+    const int TB = 256;
+    k_clear_acc<<<(unsigned)((c->n_rays + TB - 1) / TB), TB, 0, s>>>(acc, c->n_rays);
+    launch_counter()++;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = c->fwd_blocks_per_sm > 0 ? c->fwd_blocks_per_sm : 8;
+    long long grid = std::min<long long>((ng + TB - 1) / TB, (long long)sms * per_sm);
+    if (grid < 1) grid = 1;
+    k_forward_flat<WT><<<(unsigned)grid, TB, sizeof(int4) * c->n_rings, s>>>(
+        c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc);
+    launch_counter()++;
+    k_forward_finalize<<<(unsigned)((c->n_rays + TB - 1) / TB), TB, 0, s>>>(acc, c->d_proj, c->n_rays,
+                                                                          (float)c->w_scale, out, nullptr);
+    launch_counter()++;
+    USPG_CUDA(c, cudaGetLastError());
+    return USPG_OK;
+}
+
 }  // namespace uspg
+
+extern "C" uspg_status uspg_forward_project_noalloc(const uspg_ctx *cc, int32_t view, const float *f, float *out,
+                                                    uspg_stream stream)
+{
+    using namespace uspg;
+    uspg_ctx *c = const_cast<uspg_ctx *>(cc);
+    if (!c || !f || !out) return fail(c, USPG_EINVAL, "NULL argument");
+    if (c->n_rays > USPG_NOALLOC_MAX_RAYS)
+        return fail(c, USPG_EINVAL,
+                    "uspg_forward_project_noalloc: " + std::to_string(c->n_rays) + " rays per view exceed the " +
+                        std::to_string(USPG_NOALLOC_MAX_RAYS) + "-ray accumulator");
+    if (view < 0 || view >= c->scan.n_views) return fail(c, USPG_EINVAL, "bad view");
+    if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    float *acc = nullptr;
+    USPG_CUDA(c, noalloc_acc(&acc));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->dtype == USPG_F16) return fwd_noalloc_typed<__half>(c, view, f, out, acc, s);
+    if (c->dtype == USPG_BF16) return fwd_noalloc_typed<__nv_bfloat16>(c, view, f, out, acc, s);
+    return fwd_noalloc_typed<float>(c, view, f, out, acc, s);
+}

@@ -88,6 +88,7 @@ def lib():
             "uspg_kernel_launches": ([], I64),
             "uspg_mart_kernel_times": ([V, P(MartOpts), V, V, I32, P(I32), V], I32),
             "uspg_autotune": ([V, V, V], I32),
+            "uspg_forward_project_noalloc": ([V, I32, V, V, V], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -249,3 +250,13 @@ def uspg_autotune(ctx, stream=None):
     ch = np.zeros(2, np.int32)
     _check(lib().uspg_autotune(ctx, ch.ctypes.data, _stream(stream)), ctx)
     return tuple(int(x) for x in ch)
+
+
+NOALLOC_MAX_RAYS = 1 << 20
+
+
+def uspg_forward_project_noalloc(ctx, view: int, f, out, stream=None):
+    """Forward projection of one view into ``out`` with no device allocation
+    (accumulator in the library's static device array); ``f`` and ``out`` are
+    device tensors."""
+    _check(lib().uspg_forward_project_noalloc(ctx, view, _ptr(f), _ptr(out), _stream(stream)), ctx)
