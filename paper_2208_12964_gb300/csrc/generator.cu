@@ -294,7 +294,7 @@ __global__ void k_cell_count(const long long *row_ptr, const int *counts, const 
 
 // one warp per slice: width = max count over its 32 cells
 __global__ void k_slice_width(const RingEntry *rt, int n_rings, int slices_per_slab, long long n_slices,
-                              long long cps, const int *cell_cnt, int *width, uint32_t *meta)
+                              long long cps, const int *cell_cnt, int *width, uint32_t *meta, int *status)
 {
     long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -317,6 +317,7 @@ __global__ void k_slice_width(const RingEntry *rt, int n_rings, int slices_per_s
     if (lane == 0) {
         width[sl] = c;
         meta[sl] = pack_cell(slab, ring, sec0);
+        if (c > kMaxCellRays) atomicOr(status, kStatusCellRays);
     }
 }
 
@@ -340,7 +341,32 @@ __global__ void k_cell_scatter(const long long *row_ptr, const int *counts, cons
     }
 }
 
-// one thread per (slice, lane): sort the cell's entries by ray id, pad the rest
+// one thread per (slice, lane): sort the cell's entries by ray id (insertion
+// sort for short columns, heapsort beyond, so a cell crossed by very many rays
+// costs O(n log n)), pad the rest
+template <typename WT>
+__device__ void sift_down(uint32_t *ray, WT *w, long long base, int root, int n)
+{
+    for (;;) {
+        int child = 2 * root + 1;
+        if (child >= n) return;
+        long long pc = base + (long long)child * kSlice;
+        if (child + 1 < n && ray[pc + kSlice] > ray[pc]) {
+            child++;
+            pc += kSlice;
+        }
+        long long pr = base + (long long)root * kSlice;
+        if (!(ray[pc] > ray[pr])) return;
+        uint32_t tr = ray[pr];
+        ray[pr] = ray[pc];
+        ray[pc] = tr;
+        WT tw = w[pr];
+        w[pr] = w[pc];
+        w[pc] = tw;
+        root = child;
+    }
+}
+
 template <typename WT>
 __global__ void k_cell_finish(long long n_slices, const long long *slice_off, const int *width, const uint32_t *meta,
                               const RingEntry *rt, long long cps, const int *cell_cnt, uint32_t *sray, WT *sw)
@@ -355,17 +381,31 @@ __global__ void k_cell_finish(long long n_slices, const long long *slice_off, co
     if (sec < rt[ring].ng) n = cell_cnt[(long long)cell_slab(m) * cps + rt[ring].head + sec];
     long long base = slice_off[sl] + lane;
     int W = width[sl];
-    for (int q = 1; q < n; q++) {
-        uint32_t rv = sray[base + (long long)q * kSlice];
-        WT wv = sw[base + (long long)q * kSlice];
-        int p = q - 1;
-        while (p >= 0 && sray[base + (long long)p * kSlice] > rv) {
-            sray[base + (long long)(p + 1) * kSlice] = sray[base + (long long)p * kSlice];
-            sw[base + (long long)(p + 1) * kSlice] = sw[base + (long long)p * kSlice];
-            p--;
+    if (n <= 32) {
+        for (int q = 1; q < n; q++) {
+            uint32_t rv = sray[base + (long long)q * kSlice];
+            WT wv = sw[base + (long long)q * kSlice];
+            int p = q - 1;
+            while (p >= 0 && sray[base + (long long)p * kSlice] > rv) {
+                sray[base + (long long)(p + 1) * kSlice] = sray[base + (long long)p * kSlice];
+                sw[base + (long long)(p + 1) * kSlice] = sw[base + (long long)p * kSlice];
+                p--;
+            }
+            sray[base + (long long)(p + 1) * kSlice] = rv;
+            sw[base + (long long)(p + 1) * kSlice] = wv;
         }
-        sray[base + (long long)(p + 1) * kSlice] = rv;
-        sw[base + (long long)(p + 1) * kSlice] = wv;
+    } else {
+        for (int r = n / 2 - 1; r >= 0; r--) sift_down(sray, sw, base, r, n);
+        for (int end = n - 1; end > 0; end--) {
+            long long pe = base + (long long)end * kSlice;
+            uint32_t tr = sray[base];
+            sray[base] = sray[pe];
+            sray[pe] = tr;
+            WT tw = sw[base];
+            sw[base] = sw[pe];
+            sw[pe] = tw;
+            sift_down(sray, sw, base, 0, end);
+        }
     }
     for (int q = n; q < W; q++) {
         sray[base + (long long)q * kSlice] = 0;
@@ -590,7 +630,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         int *wd = c->d_slice_width + rep * n_slices;
         uint32_t *md = c->d_slice_meta + rep * n_slices;
         k_slice_width<<<nblk(n_slices * 32, 256), 256, 0, s>>>(c->d_ring, c->n_rings, c->slices_per_slab, n_slices,
-                                                               c->cells_per_slab, d_cell_cnt, wd, md);
+                                                               c->cells_per_slab, d_cell_cnt, wd, md, c->d_status);
         launch_counter()++;
         USPG_CUDA(c, exclusive_scan<int>(wd, n_slices, 1, d_rel, s));
         k_set_off<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_off + rep * n_slices, d_rel, n_slices, sell);
@@ -602,6 +642,14 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         if (tot * kSlice >= (1LL << 32)) return fail(c, USPG_EUNSUPPORTED, "a view's cell-major store exceeds 2^32 slots");
     }
     c->h_sell_base[nreps] = sell;
+    {
+        int st = 0;
+        USPG_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st & kStatusCellRays) {
+            USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+            return fail(c, USPG_EUNSUPPORTED, "a cell is crossed by more than 2047 rays of one view");
+        }
+    }
     if ((size_t)(sell + kSlice) > c->cap_sell) {
         cudaFree(c->d_sray);
         cudaFree(c->d_sw);

@@ -31,6 +31,8 @@ constexpr int kStatusCountMismatch = 1;
 constexpr int kStatusRing0Overflow = 2;
 constexpr int kStatusBounds = 4;
 constexpr int kStatusTimeout = 8;
+constexpr int kStatusCellRays = 16;
+constexpr int kMaxCellRays = 2047;  // rays of one view through one cell (11-bit lane count)
 
 // Stored cell index of a representative row: slab (10 b) | ring (10 b) | sector (12 b).
 __host__ __device__ inline uint32_t pack_cell(int slab, int ring, int sector)
