@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--coeff-dtype", default="f32", choices=["f32", "f16", "bf16"])
     return ap.parse_args()
 
 
@@ -138,7 +139,8 @@ def run_ours(args, rank, world, local):
     proj_host = synth.projections(spec)
     n_views, n_rays = proj_host.shape
     iters, lam = spec["iterations"], spec["lam"]
-    g, s, o, _ = uspg.descs_from_spec(spec)
+    dt = {"f32": uspg.F32, "f16": uspg.F16, "bf16": uspg.BF16}[args.coeff_dtype]
+    g, s, o, _ = uspg.descs_from_spec(spec, dtype=dt)
     ctx = uspg.uspg_create(g, s, o)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
@@ -251,7 +253,7 @@ def run_ours(args, rank, world, local):
         t_max = float(tt[0])
         if e2e:
             e2e = (float(tt[1]), e2e[1], e2e[2])
-    info = dict(tuned=tuned, stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
+    info = dict(weight_bytes=4 if args.coeff_dtype == "f32" else 2, tuned=tuned, stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
                 ms_build=ms_build, ms_mart=ms_mart, ms_resample=ms_resample, fw=fw, bw=bw, e2e=e2e, spec=spec,
                 proj=proj_host)
     uspg.uspg_destroy(ctx)
@@ -266,7 +268,7 @@ def roofline(info):
     n_rays = st["n_rays"]
     reps = st["n_reps"]
     nnz_view = st["nnz_all_views"] / st["n_views"]
-    wb = 4
+    wb = info.get("weight_bytes", 4)
     # forward: stream the representative rows (index + weight), row pointers,
     # projections in, per-ray log ratio out; the image (25 MB) is L2-resident
     fwd_bytes = nnz_view * (4 + wb) + n_rays * (8 + 4 + 4)
@@ -352,7 +354,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "rings": info["spec"]["n_rings"],
                        "slabs": info["spec"]["n_slabs"], "views": st["n_views"], "detector": [256, 256],
-                       "iterations": info["spec"]["iterations"], "schedule": "per_view", "coeff_dtype": "f32",
+                       "iterations": info["spec"]["iterations"], "schedule": "per_view", "coeff_dtype": args.coeff_dtype,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}",
                        "step": "coefficient build + MART + resample",
                        "launch_shape": dict(zip(["fwd_blocks_per_sm", "bwd_blocks_per_sm"], info["tuned"]))},

@@ -59,7 +59,8 @@ __global__ void k_mirror_rows(int n_reps, int n_u, int n_v, int n_rays, int mirr
                               const long long *row_ptr, int *counts, uint32_t *idx, double *w64, int *status)
 {
     long long half = (long long)(n_v - mirror_from) * n_u;
-    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per row
+    int lane = threadIdx.x & 31;
     if (gid >= (long long)n_reps * half) return;
     int rep = (int)(gid / half);
     int q = (int)(gid % half);
@@ -69,19 +70,19 @@ __global__ void k_mirror_rows(int n_reps, int n_u, int n_v, int n_rays, int mirr
     long long sb = row_ptr[src], db = row_ptr[dst], de = row_ptr[dst + 1];
     int n = counts[src];
     if (db + n > de) {  // the bound is the source's, so this cannot happen
-        flag(status, kStatusBounds);
+        if (lane == 0) flag(status, kStatusBounds);
         n = (int)(de - db);
     }
-    for (int k = 0; k < n; k++) {
+    for (int k = lane; k < n; k += 32) {
         uint32_t pc = idx[sb + k];
         idx[db + k] = pack_cell(n_slabs - 1 - cell_slab(pc), cell_ring(pc), cell_sector(pc));
         w64[db + k] = w64[sb + k];
     }
-    for (long long k = db + n; k < de; k++) {
+    for (long long k = db + n + lane; k < de; k += 32) {
         idx[k] = 0;
         w64[k] = 0.0;
     }
-    counts[dst] = n;
+    if (lane == 0) counts[dst] = n;
 }
 
 // Exact row lengths (the FP64 walk without storing); used only when a row
@@ -282,14 +283,16 @@ __device__ __forceinline__ long long rep_cell_id(const RingEntry *rt, long long 
     return (long long)cell_slab(pc) * cps + rt[cell_ring(pc)].head + cell_sector(pc);
 }
 
+// one warp per row (coalesced entries)
 __global__ void k_cell_count(const long long *row_ptr, const int *counts, const uint32_t *idx, int n_rays,
                              const RingEntry *rt, long long cps, int *cell_cnt)
 {
-    long long ray = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
     if (ray >= n_rays) return;
     long long b = row_ptr[ray];
     int n = counts[ray];
-    for (int q = 0; q < n; q++) atomicAdd(&cell_cnt[rep_cell_id(rt, cps, idx[b + q])], 1);
+    for (int q = lane; q < n; q += 32) atomicAdd(&cell_cnt[rep_cell_id(rt, cps, idx[b + q])], 1);
 }
 
 // one warp per slice: width = max count over its 32 cells
@@ -326,11 +329,12 @@ __global__ void k_cell_scatter(const long long *row_ptr, const int *counts, cons
                                int n_rays, const RingEntry *rt, long long cps, int slices_per_slab,
                                const long long *slice_off, int *cell_fill, uint32_t *sray, WT *sw)
 {
-    long long ray = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int wl = threadIdx.x & 31;
     if (ray >= n_rays) return;
     long long b = row_ptr[ray];
     int n = counts[ray];
-    for (int q = 0; q < n; q++) {
+    for (int q = wl; q < n; q += 32) {  // one warp per row
         uint32_t pc = idx[b + q];
         int lane;
         long long sl = rep_cell_slice(rt, slices_per_slab, pc, &lane);
@@ -574,7 +578,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaGetLastError());
         if (mirror_from > 0) {
             long long nm = (long long)nreps * (g.n_v - mirror_from) * g.n_u;
-            k_mirror_rows<<<nblk(nm, 256), 256, 0, s>>>(nreps, g.n_u, g.n_v, g.n_rays, mirror_from, g.n_slabs,
+            k_mirror_rows<<<nblk(nm * 32, 256), 256, 0, s>>>(nreps, g.n_u, g.n_v, g.n_rays, mirror_from, g.n_slabs,
                                                         c->d_row_ptr, d_counts, c->d_idx, c->d_w64, c->d_status);
             launch_counter()++;
             USPG_CUDA(c, cudaGetLastError());
@@ -624,7 +628,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         const long long *rp = c->d_row_ptr + (long long)rep * c->n_rays;
         const int *cn = d_counts + (long long)rep * c->n_rays;
         USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
-        k_cell_count<<<nblk(c->n_rays, 128), 128, 0, s>>>(rp, cn, c->d_idx, c->n_rays, c->d_ring, c->cells_per_slab,
+        k_cell_count<<<nblk((long long)c->n_rays * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, c->n_rays, c->d_ring, c->cells_per_slab,
                                                           d_cell_cnt);
         launch_counter()++;
         int *wd = c->d_slice_width + rep * n_slices;
@@ -685,10 +689,10 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         const long long *so = c->d_slice_off + rep * n_slices;
         USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
         USPG_CUDA(c, cudaMemsetAsync(d_cell_fill, 0, sizeof(int) * c->n_cells, s));
-        k_cell_count<<<nblk(c->n_rays, 128), 128, 0, s>>>(rp, cn, c->d_idx, c->n_rays, c->d_ring, c->cells_per_slab,
+        k_cell_count<<<nblk((long long)c->n_rays * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, c->n_rays, c->d_ring, c->cells_per_slab,
                                                           d_cell_cnt);
         launch_counter()++;
-        k_cell_scatter<WT><<<nblk(c->n_rays, 128), 128, 0, s>>>(rp, cn, c->d_idx, (const WT *)c->d_w, c->n_rays,
+        k_cell_scatter<WT><<<nblk((long long)c->n_rays * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, (const WT *)c->d_w, c->n_rays,
                                                                 c->d_ring, c->cells_per_slab, c->slices_per_slab, so,
                                                                 d_cell_fill, c->d_sray, (WT *)c->d_sw);
         launch_counter()++;

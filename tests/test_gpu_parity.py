@@ -285,3 +285,47 @@ def test_errors_and_degenerate_inputs(torch_cuda):
     f0 = np.full(ow.n_cells, 0.7, np.float32)
     got = _run_mart(gw, np.ones((3, 9), np.float32), f0, 0, 0.5, 1)
     assert np.array_equal(got, f0)
+
+
+# -------------------------------------------------------------- precision ---
+
+@pytest.mark.parametrize("dtype,wtol", [("f16", 2 ** -10), ("bf16", 2 ** -7)])
+def test_reduced_precision_rows(torch_cuda, dtype, wtol):
+    """FP16/BF16 stores keep the index lists exact; each weight is the FP64
+    length rounded once to the storage format (relative error <= one unit in
+    the last place; FP16 weights are stored in units of the cell size)."""
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.cone_workload(12, 8, 18, 24, noise=False)
+    g = Gpu(spec, dtype=uspg.F16 if dtype == "f16" else uspg.BF16).build()
+    o = oracle_for(spec)
+    rng = np.random.default_rng(21)
+    for _ in range(300):
+        k, ray = int(rng.integers(18)), int(rng.integers(24 * 24))
+        gc, gw = g.row(k, ray)
+        oc, ow = o.row(k, ray)
+        assert np.array_equal(gc, oc)
+        big = ow > 1e-4 * spec["r"]  # below that, FP16 subnormals round coarser
+        if big.any():
+            assert np.max(np.abs(gw[big] - ow[big]) / ow[big]) <= wtol
+
+
+def test_reduced_precision_mart_error(torch_cuda):
+    """Image error of the per-view MART against the FP64 oracle for FP32, FP16
+    and BF16 coefficient stores (FP32 accumulation throughout)."""
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.cone_workload(16, 12, 24, 32, iterations=3, lam=0.1, seed=9)
+    proj = synth.projections(spec)
+    o = oracle_for(spec)
+    f0 = np.ones(o.n_cells)
+    ref = o.mart_per_view(proj, f0, 3, 0.1)
+    err = {}
+    for name, dt in (("f32", uspg.F32), ("f16", uspg.F16), ("bf16", uspg.BF16)):
+        g = Gpu(spec, dtype=dt).build()
+        got = _run_mart(g, proj, f0, 3, 0.1, 1)
+        err[name] = rel_l2(got, ref)
+    print("rel-L2 vs FP64 oracle:", err)
+    assert err["f32"] < TOL_IMG
+    assert err["f16"] < 2e-3
+    assert err["bf16"] < 1e-2
