@@ -337,11 +337,93 @@ def run_reference(args, rank, world):
     return 0
 
 
+def batch_specs(n=64, seed=4):
+    """64 independent 2D parallel-beam reconstructions of uneven size: rings
+    from {64, 128, 256, 512}, views from {18, 36, 90, 180} over a half turn,
+    2R+1 detector bins, seeded ellipse phantoms, 10 per-view iterations."""
+    from paper_2208_12964_gb300 import synth
+
+    g = synth.Stream(seed)
+    out = []
+    for i in range(n):
+        a, b = g.u(2)
+        R = (64, 128, 256, 512)[int(a * 4)]
+        V = (18, 36, 90, 180)[int(b * 4)]
+        out.append(synth.parallel_workload(R, V, 2 * R + 1, seed=100 + i, iterations=10, lam=0.2))
+    return out
+
+
+def run_batched(args, rank, world, local):
+    import torch
+
+    from paper_2208_12964_gb300 import synth, uspg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    specs = batch_specs()
+    ctxs = []
+    for spc in specs:
+        g, s, o, _ = uspg.descs_from_spec(spc)
+        c = uspg.uspg_create(g, s, o)
+        uspg.uspg_build_coeffs(c, sp)
+        uspg.uspg_set_projections(c, synth.projections(spc), False, sp)
+        uspg.uspg_fill_image(c, 1.0, sp)
+        ctxs.append(c)
+    torch.cuda.synchronize(dev)
+    opts, _k = uspg.mart_opts(10, 0.2, uspg.PER_VIEW)
+    b = uspg.uspg_batch_create(ctxs, opts, sp)
+    info = uspg.uspg_batch_info(b)
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        uspg.uspg_batch_run(b, sp)
+    torch.cuda.synchronize(dev)
+    launches0 = uspg.uspg_kernel_launches()
+    with ClockSampler(local) as clk:
+        t = timed(lambda: uspg.uspg_batch_run(b, sp), args.steps)
+    launches = uspg.uspg_kernel_launches() - launches0
+
+    def sequential():
+        for c in ctxs:
+            uspg.uspg_mart(c, opts, sp)
+
+    sequential()
+    t_seq = timed(sequential, 1)
+    uspg.uspg_batch_destroy(b)
+    for c in ctxs:
+        uspg.uspg_destroy(c)
+    upd = info["updates_per_run"]
+    line = {"metric": METRIC, "value": upd * args.steps / (t * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch-2d-64", "instances": len(specs),
+                       "rings": sorted({s_["n_rings"] for s_ in specs}), "views": sorted({s_["n_views"] for s_ in specs}),
+                       "iterations": 10, "graph_kernel_nodes": info["kernel_nodes"], "global_steps": info["steps"],
+                       "step": "one batched run (10 per-view sweeps of every instance)"},
+            "sequential": {"value": upd / (t_seq * 1e-3), "ms": t_seq,
+                           "how": "the same instances, uspg_mart one after another (one graph each)"},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch-2d-64":
+        return run_batched(args, rank, world, local)
     info = run_ours(args, rank, world, local)
     if rank != 0:
         return 0

@@ -196,6 +196,31 @@ uspg_status uspg_forward_project(uspg_ctx *ctx, int32_t view, float *out, uspg_s
  * fewer than requested).  Synchronous. */
 uspg_status uspg_mart_sweeps(uspg_ctx *ctx, int32_t *sweeps);
 
+/* --- batched reconstructions ---------------------------------------------------- */
+
+typedef struct uspg_batch uspg_batch;
+
+/* Batched per-view MART (Sec. III.D) over n independent contexts of any sizes
+ * (grids, view counts, detectors).  Every context needs built coefficients
+ * and projections, and all must store coefficients in one dtype; each runs
+ * opts->iterations sweeps of its own views from its current image, exactly as
+ * uspg_mart with the same opts would (view order 0..p-1).  The contexts
+ * advance together: global step t runs view step t of every context that has
+ * one, as three launches covering all of them (each context gets blocks in
+ * proportion to its work per view); all steps are captured in one CUDA graph.
+ * Creation tunes the blocks-per-work ratio on the first steps (images are
+ * saved and restored) and captures the graph.  The contexts must stay alive,
+ * and must not rebuild their coefficients, until uspg_batch_destroy.
+ * Synchronous.  opts->view_order, view_steps and stop_tol are ignored;
+ * errors are reported through uspg_last_error(NULL). */
+uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_opts *opts, uspg_stream stream,
+                              uspg_batch **out);
+/* One batched run (one graph launch) on `stream`. */
+uspg_status uspg_batch_run(uspg_batch *batch, uspg_stream stream);
+/* Ray-cell updates of one run, kernel nodes in the graph, global steps. */
+uspg_status uspg_batch_info(const uspg_batch *batch, int64_t *updates_per_run, int64_t *kernel_nodes, int64_t *steps);
+void uspg_batch_destroy(uspg_batch *batch);
+
 /* --- display (Sec. II.B) ------------------------------------------------------- */
 
 /* USPG -> Cartesian.  POINT: an nx x ny image over [-R, R]^2 per slab, each

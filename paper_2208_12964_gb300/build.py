@@ -25,6 +25,7 @@ UNITS = {
     "generator.cu": ["-fmad=false"],
     "mart.cu": [],
     "resample.cu": ["-fmad=false"],
+    "batch.cu": [],
 }
 
 

@@ -1,0 +1,348 @@
+// Batched per-view MART over many independent reconstructions (instances of
+// uneven size: grids, view counts, detectors).  Instance i runs its own
+// per-view schedule (Sec. III.D): view step t of instance i is view
+// t mod p_i of sweep t div p_i, for t < iterations * p_i.  The instances
+// advance together: global step t is three launches (forward sums, ray
+// ratios, cell correction) whose 2D grid covers every instance still running
+// (blockIdx.y = instance; each instance gets a number of blocks proportional
+// to its work per view).  All global steps are captured in one CUDA graph,
+// so a batch of small instances costs one graph launch instead of thousands
+// of kernel launches.  The blocks-per-work ratio is tuned on creation.
+#include "internal.cuh"
+#include "device.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace uspg {
+
+struct BatchInst {
+    const uint32_t *idx;
+    const void *w;
+    const uint32_t *grp_ray;
+    const long long *rep_g0;  // [reps] first 8-entry group of each representative
+    const long long *rep_ng;  // [reps] groups of each representative
+    float *f;
+    const RingEntry *rt;
+    float *sacc;
+    float *res;
+    const float *proj;
+    const long long *slice_off;
+    const uint32_t *slice_meta;
+    const uint16_t *lane_desc;
+    const uint32_t *cray;
+    const void *cw;
+    const long long *rep_sell;  // [reps] first cell-major slot of each representative
+    const int *view_rep;        // [views]
+    const int *view_mg;         // [views]
+    long long cps, S, steps;
+    int n_rings, n_rays, n_views, fwd_blocks, bwd_blocks;
+    float w_scale;
+};
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_batch_forward(const BatchInst *__restrict__ inst, long long step)
+{
+    extern __shared__ int4 tab[];
+    const BatchInst &I = inst[blockIdx.y];
+    if (step >= I.steps || (int)blockIdx.x >= I.fwd_blocks) return;  // block-uniform
+    int view = (int)(step % I.n_views);
+    int rep = I.view_rep[view];
+    fill_tab(tab, I.rt, I.n_rings, I.view_mg[view], threadIdx.x, blockDim.x);
+    __syncthreads();
+    fwd_groups<WT>(I.idx, (const WT *)I.w, I.grp_ray, I.rep_g0[rep], I.rep_ng[rep], I.f, tab, I.cps, I.sacc,
+                   ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((long long)I.fwd_blocks * blockDim.x) >> 5,
+                   threadIdx.x & 31);
+}
+
+__global__ void k_batch_finalize(const BatchInst *__restrict__ inst, long long step)
+{
+    const BatchInst &I = inst[blockIdx.y];
+    if (step >= I.steps) return;
+    int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= I.n_rays) return;
+    int view = (int)(step % I.n_views);
+    finalize_ray(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.w_scale, nullptr, I.res);
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_batch_backward(const BatchInst *__restrict__ inst, long long step,
+                                                        float lambda)
+{
+    const BatchInst &I = inst[blockIdx.y];
+    if (step >= I.steps || (int)blockIdx.x >= I.bwd_blocks) return;
+    int view = (int)(step % I.n_views);
+    int rep = I.view_rep[view];
+    bwd_slices<WT>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
+                   I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt, I.view_mg[view], I.cps,
+                   I.S, lambda, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                   ((long long)I.bwd_blocks * blockDim.x) >> 5, threadIdx.x & 31);
+}
+
+}  // namespace uspg
+
+using namespace uspg;
+
+struct uspg_batch {
+    std::vector<uspg_ctx *> ctx;
+    std::vector<BatchInst> host;
+    BatchInst *d_inst = nullptr;
+    void *d_tables = nullptr;  // per-instance rep/view tables
+    int dtype = USPG_F32;
+    double lambda = 0.1;
+    long long max_steps = 0;
+    int max_rings = 0, max_rays = 0;
+    long long nnz_per_run = 0;  // ray-cell updates of one run
+    std::vector<long long> groups_view, slices_view;  // per instance: mean groups / slices per view
+    double fwd_ratio = 0, bwd_ratio = 0;               // blocks per unit of work (tuned)
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;
+};
+
+// per-instance block counts from the current ratios; returns the max of each
+static void assign_blocks(uspg_batch *b, int &mf, int &mb)
+{
+    mf = mb = 1;
+    for (size_t i = 0; i < b->host.size(); i++) {
+        long long fb = (long long)(b->fwd_ratio * (double)b->groups_view[i]) + 1;
+        long long bb = (long long)(b->bwd_ratio * (double)b->slices_view[i]) + 1;
+        long long fmax = (b->groups_view[i] + 255) / 256 + 1, bmax = (b->slices_view[i] + 7) / 8 + 1;
+        b->host[i].fwd_blocks = (int)std::min(fb, fmax);
+        b->host[i].bwd_blocks = (int)std::min(bb, bmax);
+        mf = std::max(mf, b->host[i].fwd_blocks);
+        mb = std::max(mb, b->host[i].bwd_blocks);
+    }
+}
+
+// block counts into the device instance table (synchronous)
+static cudaError_t upload(uspg_batch *b, int &mf, int &mb)
+{
+    assign_blocks(b, mf, mb);
+    return cudaMemcpy(b->d_inst, b->host.data(), sizeof(BatchInst) * b->host.size(), cudaMemcpyHostToDevice);
+}
+
+template <typename WT>
+static cudaError_t enqueue_steps(uspg_batch *b, int mf, int mb, long long s0, long long s1, cudaStream_t s,
+                                 int64_t *nodes)
+{
+    unsigned n = (unsigned)b->host.size();
+    size_t smem = sizeof(int4) * b->max_rings;
+    for (long long t = s0; t < s1; t++) {
+        k_batch_forward<WT><<<dim3(mf, n), 256, smem, s>>>(b->d_inst, t);
+        k_batch_finalize<<<dim3((b->max_rays + 255) / 256, n), 256, 0, s>>>(b->d_inst, t);
+        k_batch_backward<WT><<<dim3(mb, n), 256, 0, s>>>(b->d_inst, t, (float)b->lambda);
+        if (nodes) *nodes += 3;
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t enqueue(uspg_batch *b, int mf, int mb, long long s0, long long s1, cudaStream_t s, int64_t *nodes)
+{
+    if (b->dtype == USPG_F16) return enqueue_steps<__half>(b, mf, mb, s0, s1, s, nodes);
+    if (b->dtype == USPG_BF16) return enqueue_steps<__nv_bfloat16>(b, mf, mb, s0, s1, s, nodes);
+    return enqueue_steps<float>(b, mf, mb, s0, s1, s, nodes);
+}
+
+extern "C" {
+
+void uspg_batch_destroy(uspg_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_tables);
+    delete b;
+}
+
+uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_opts *o, uspg_stream stream,
+                              uspg_batch **out)
+{
+    if (!out || !ctxs || !o || n < 1) return fail(nullptr, USPG_EINVAL, "batch: NULL argument or n < 1");
+    *out = nullptr;
+    if (o->schedule != USPG_PER_VIEW || o->update_rule != USPG_POWER)
+        return fail(nullptr, USPG_EUNSUPPORTED, "batch: per-view schedule with the power update only");
+    if (o->iterations < 1 || !(o->lambda > 0.0 && o->lambda < 2.0))
+        return fail(nullptr, USPG_EINVAL, "batch: iterations >= 1 and lambda in (0, 2)");
+    uspg_batch *b = new uspg_batch();
+    b->lambda = o->lambda;
+    b->dtype = ctxs[0]->dtype;
+    // per-instance tables: rep_g0, rep_ng, rep_sell (int64 [reps]) and view_rep, view_mg (int [views])
+    std::vector<long long> off_tab(n);
+    long long bytes = 0;
+    for (int i = 0; i < n; i++) {
+        uspg_ctx *c = ctxs[i];
+        if (!c || !c->built || !c->have_proj) {
+            uspg_batch_destroy(b);
+            return fail(nullptr, USPG_ENOTREADY, "batch: every context needs coefficients and projections");
+        }
+        if (c->dtype != b->dtype) {
+            uspg_batch_destroy(b);
+            return fail(nullptr, USPG_EINVAL, "batch: all contexts must store coefficients in one dtype");
+        }
+        off_tab[i] = bytes;
+        bytes += 8LL * 3 * c->n_reps + 4LL * 2 * c->scan.n_views;
+        bytes = (bytes + 15) & ~15LL;
+    }
+    std::vector<unsigned char> tab(bytes);
+    b->ctx.assign(ctxs, ctxs + n);
+    b->host.resize(n);
+    b->groups_view.resize(n);
+    b->slices_view.resize(n);
+    if (cudaMalloc(&b->d_tables, bytes + 16) != cudaSuccess || cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess) {
+        uspg_batch_destroy(b);
+        return fail(nullptr, USPG_ENOMEM, "batch: device tables");
+    }
+    for (int i = 0; i < n; i++) {
+        uspg_ctx *c = ctxs[i];
+        int R = c->n_reps, V = c->scan.n_views;
+        long long *g0 = (long long *)(tab.data() + off_tab[i]);
+        long long *ng = g0 + R, *sb = ng + R;
+        int *vr = (int *)(sb + R), *vm = vr + V;
+        long long gsum = 0;
+        for (int r = 0; r < R; r++) {
+            g0[r] = c->h_rep_entry0[r] / kRowPad;
+            ng[r] = (c->h_rep_entry0[r + 1] - c->h_rep_entry0[r]) / kRowPad;
+            sb[r] = c->h_sell_base[r];
+        }
+        for (int k = 0; k < V; k++) {
+            vr[k] = c->rep_of_view[k];
+            vm[k] = c->m_of_view[k] % c->G;
+            gsum += ng[vr[k]];
+        }
+        unsigned char *dt = (unsigned char *)b->d_tables + off_tab[i];
+        BatchInst &I = b->host[i];
+        I.idx = c->d_idx;
+        I.w = c->d_w;
+        I.grp_ray = c->d_grp_ray;
+        I.rep_g0 = (const long long *)dt;
+        I.rep_ng = I.rep_g0 + R;
+        I.rep_sell = I.rep_ng + R;
+        I.view_rep = (const int *)(I.rep_sell + R);
+        I.view_mg = I.view_rep + V;
+        I.f = c->d_f;
+        I.rt = c->d_ring;
+        I.sacc = c->d_sacc;
+        I.res = c->d_res;
+        I.proj = c->d_proj;
+        I.slice_off = c->d_slice_off;
+        I.slice_meta = c->d_slice_meta;
+        I.lane_desc = c->d_lane_desc;
+        I.cray = c->d_cm_ray;
+        I.cw = c->d_cm_w;
+        I.cps = c->cells_per_slab;
+        I.S = c->slices_per_rep;
+        I.steps = (long long)o->iterations * V;
+        I.n_rings = c->n_rings;
+        I.n_rays = c->n_rays;
+        I.n_views = V;
+        I.w_scale = (float)c->w_scale;
+        b->groups_view[i] = std::max<long long>(1, gsum / V);
+        b->slices_view[i] = std::max<long long>(1, I.S);
+        b->max_steps = std::max(b->max_steps, I.steps);
+        b->max_rings = std::max(b->max_rings, c->n_rings);
+        b->max_rays = std::max(b->max_rays, c->n_rays);
+        b->nnz_per_run += (long long)o->iterations * c->nnz_all_views;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(b->d_tables, tab.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        uspg_batch_destroy(b);
+        return fail(nullptr, USPG_ECUDA, "batch: table upload");
+    }
+    // tune the blocks-per-work ratios on the first steps; images are saved
+    // and restored so the instances' state does not change
+    std::vector<float *> saved(n, nullptr);
+    for (int i = 0; i < n; i++) {
+        if (cudaMallocAsync(&saved[i], sizeof(float) * ctxs[i]->n_cells, s) != cudaSuccess ||
+            cudaMemcpyAsync(saved[i], ctxs[i]->d_f, sizeof(float) * ctxs[i]->n_cells, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess) {
+            uspg_batch_destroy(b);
+            return fail(nullptr, USPG_ENOMEM, "batch: tuning scratch");
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const double fr[4] = {1.0 / 8192, 1.0 / 2048, 1.0 / 512, 1.0 / 128};  // blocks per 8-entry group
+    const double br[4] = {1.0 / 2048, 1.0 / 512, 1.0 / 128, 1.0 / 32};    // blocks per slice
+    long long probe = std::min<long long>(b->max_steps, 4);
+    float best = 1e30f;
+    double bf = fr[1], bb = br[1];
+    for (double a : fr)
+        for (double c2 : br) {
+            b->fwd_ratio = a;
+            b->bwd_ratio = c2;
+            int mf, mb;
+            cudaStreamSynchronize(s);
+            if (upload(b, mf, mb) != cudaSuccess) continue;
+            enqueue(b, mf, mb, 0, probe, s, nullptr);  // warm
+            cudaEventRecord(e0, s);
+            enqueue(b, mf, mb, 0, probe, s, nullptr);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bf = a;
+                bb = c2;
+            }
+        }
+    b->fwd_ratio = bf;
+    b->bwd_ratio = bb;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < n; i++) {
+        cudaMemcpyAsync(ctxs[i]->d_f, saved[i], sizeof(float) * ctxs[i]->n_cells, cudaMemcpyDeviceToDevice, s);
+        cudaFreeAsync(saved[i], s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        uspg_batch_destroy(b);
+        return fail(nullptr, USPG_ECUDA, "batch: tuning failed");
+    }
+    // capture all global steps into one graph
+    int mf = 1, mb = 1;
+    if (upload(b, mf, mb) != cudaSuccess) {
+        uspg_batch_destroy(b);
+        return fail(nullptr, USPG_ECUDA, "batch: instance table upload");
+    }
+    cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        uspg_batch_destroy(b);
+        return fail(nullptr, USPG_ECUDA, "batch: capture");
+    }
+    int64_t nodes = 0;
+    cudaError_t ce = enqueue(b, mf, mb, 0, b->max_steps, b->cap, &nodes);
+    cudaError_t ee = cudaStreamEndCapture(b->cap, &b->graph);
+    if (ce || ee || cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
+        uspg_batch_destroy(b);
+        return fail(nullptr, USPG_ECUDA, "batch: graph capture or instantiation failed");
+    }
+    b->nodes = nodes;
+    *out = b;
+    return USPG_OK;
+}
+
+uspg_status uspg_batch_run(uspg_batch *b, uspg_stream stream)
+{
+    if (!b) return fail(nullptr, USPG_EINVAL, "NULL batch");
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, USPG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    launch_counter() += b->nodes;
+    return USPG_OK;
+}
+
+uspg_status uspg_batch_info(const uspg_batch *b, int64_t *updates_per_run, int64_t *kernel_nodes, int64_t *steps)
+{
+    if (!b) return fail(nullptr, USPG_EINVAL, "NULL batch");
+    if (updates_per_run) *updates_per_run = b->nnz_per_run;
+    if (kernel_nodes) *kernel_nodes = b->nodes;
+    if (steps) *steps = b->max_steps;
+    return USPG_OK;
+}
+
+}  // extern "C"

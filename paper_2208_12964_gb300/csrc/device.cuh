@@ -1,0 +1,255 @@
+// Device building blocks of the per-view MART kernels, shared by the
+// single-reconstruction kernels (mart.cu) and the batched kernels (batch.cu).
+#pragma once
+
+#include "internal.cuh"
+
+namespace uspg {
+
+// ---- weight loads ------------------------------------------------------------
+
+__device__ __forceinline__ float load_w1(const float *w, long long q) { return w[q]; }
+__device__ __forceinline__ float load_w1(const __half *w, long long q) { return __half2float(w[q]); }
+__device__ __forceinline__ float load_w1(const __nv_bfloat16 *w, long long q) { return __bfloat162float(w[q]); }
+
+// rotated cell id of a stored entry; tab[ring] = {head, ng, q, 0}
+__device__ __forceinline__ long long rot_cell(const int4 *tab, long long cps, uint32_t pc)
+{
+    int4 t = tab[cell_ring(pc)];
+    int s = cell_sector(pc) + t.z;
+    s = s >= t.y ? s - t.y : s;
+    return (long long)cell_slab(pc) * cps + t.x + s;
+}
+
+__device__ __forceinline__ void fill_tab(int4 *tab, const RingEntry *rt, int n_rings, int mG, int tid, int nt)
+{
+    for (int i = tid; i < n_rings; i += nt) {
+        RingEntry e = rt[i];
+        tab[i] = make_int4(e.head, e.ng, mG * e.step, 0);
+    }
+}
+
+__device__ __forceinline__ void load_w8(const float *w, long long q, float o[8])
+{
+    float4 a = __ldcs((const float4 *)(w + q)), b = __ldcs((const float4 *)(w + q + 4));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void load_w8(const __half *w, long long q, float o[8])
+{
+    uint4 u = __ldcs((const uint4 *)(w + q));
+    const __half2 *h = (const __half2 *)&u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float2 v = __half22float2(h[i]);
+        o[2 * i] = v.x;
+        o[2 * i + 1] = v.y;
+    }
+}
+__device__ __forceinline__ void load_w8(const __nv_bfloat16 *w, long long q, float o[8])
+{
+    uint4 u = __ldcs((const uint4 *)(w + q));
+    const __nv_bfloat162 *h = (const __nv_bfloat162 *)&u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float2 v = __bfloat1622float2(h[i]);
+        o[2 * i] = v.x;
+        o[2 * i + 1] = v.y;
+    }
+}
+__device__ __forceinline__ float load_cs(const float *w, long long q) { return __ldcs(w + q); }
+__device__ __forceinline__ float load_cs(const __half *w, long long q)
+{
+    return __half2float(__ushort_as_half(__ldcs((const unsigned short *)(w + q))));
+}
+__device__ __forceinline__ float load_cs(const __nv_bfloat16 *w, long long q)
+{
+    return __bfloat162float(__ushort_as_bfloat16(__ldcs((const unsigned short *)(w + q))));
+}
+
+template <typename WT>
+struct Group8 {
+    uint32_t c[8];
+    float w[8];
+    uint32_t ray;
+};
+
+template <typename WT>
+__device__ __forceinline__ void load_group(Group8<WT> &G, const uint32_t *idx, const WT *w, const uint32_t *grp_ray,
+                                           long long g, bool valid)
+{
+    if (valid) {
+        long long q = g * kRowPad;
+        uint4 ia = __ldcs((const uint4 *)(idx + q)), ib = __ldcs((const uint4 *)(idx + q + 4));
+        load_w8(w, q, G.w);
+        G.ray = __ldcs(grp_ray + g);
+        G.c[0] = ia.x; G.c[1] = ia.y; G.c[2] = ia.z; G.c[3] = ia.w;
+        G.c[4] = ib.x; G.c[5] = ib.y; G.c[6] = ib.z; G.c[7] = ib.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            G.c[i] = 0;
+            G.w[i] = 0.0f;
+        }
+        G.ray = 0xffffffffu;
+    }
+}
+
+// Forward ray sums over the 8-entry groups [0, n_groups) of one
+// representative's rows (group g starts at entry (g0 + g) * 8), by warps
+// w = wg, wg + W, ...; partial sums of each ray segment go to sacc[ray].
+// tab: ring table {head, ng, shift} of the view.  Each lane takes one group;
+// the next chunk's stream loads are issued before the current chunk's image
+// gathers, and lanes of the same ray are combined by a segmented shuffle sum.
+template <typename WT>
+__device__ __forceinline__ void fwd_groups(const uint32_t *__restrict__ idx, const WT *__restrict__ w,
+                                           const uint32_t *__restrict__ grp_ray, long long g0, long long n_groups,
+                                           const float *__restrict__ f, const int4 *tab, long long cps,
+                                           float *__restrict__ sacc, long long wg, long long W, int lane)
+{
+    const long long step = W * 32;
+    long long base = wg * 32;
+    if (base >= n_groups) return;
+    Group8<WT> cur, nxt;
+    load_group(cur, idx, w, grp_ray, g0 + base + lane, base + lane < n_groups);
+    for (; base < n_groups; base += step) {
+        long long nb = base + step;
+        load_group(nxt, idx, w, grp_ray, g0 + nb + lane, nb + lane < n_groups);
+        float gv[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) gv[i] = cur.w[i] != 0.0f ? __ldg(f + rot_cell(tab, cps, cur.c[i])) : 0.0f;
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; i++) acc = fmaf(cur.w[i], gv[i], acc);
+        uint32_t ray = cur.ray;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            float v2 = __shfl_down_sync(0xffffffffu, acc, o);
+            uint32_t r2 = __shfl_down_sync(0xffffffffu, ray, o);
+            if (lane + o < 32 && r2 == ray) acc += v2;
+        }
+        uint32_t rprev = __shfl_up_sync(0xffffffffu, ray, 1);
+        if (ray != 0xffffffffu && (lane == 0 || rprev != ray)) atomicAdd(&sacc[ray], acc);
+        cur = nxt;
+    }
+}
+
+// ln(P/Pbar) of one ray from its accumulated sum; clears the accumulator.
+// NaN marks a ray to skip (empty row or zero sum), -inf a ray with P = 0.
+__device__ __forceinline__ void finalize_ray(float *__restrict__ sacc, const float *__restrict__ proj, int ray,
+                                             float w_scale, float *__restrict__ out_s, float *__restrict__ out_res)
+{
+    float sv = sacc[ray] * w_scale;
+    sacc[ray] = 0.0f;
+    if (out_s) out_s[ray] = sv;
+    if (out_res) {
+        float res;
+        if (!(sv > 0.0f)) {
+            res = __int_as_float(0x7fc00000);
+        } else {
+            float p = proj[ray];
+            res = p > 0.0f ? logf(p / sv) : -INFINITY;
+        }
+        out_res[ray] = res;
+    }
+}
+
+struct SliceDesc {
+    uint32_t d, m, off;
+};
+
+__device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_off, long long base,
+                                          const uint32_t *slice_meta, const uint16_t *lane_desc, long long sl,
+                                          long long n_slices, int lane)
+{
+    if (sl < n_slices) {
+        D.d = lane_desc[sl * 32 + lane];
+        D.m = slice_meta[sl];
+        D.off = (uint32_t)(slice_off[sl] - base);
+    } else {
+        D.d = 0;
+        D.m = 0;
+        D.off = 0;
+    }
+}
+
+// rows 0..R-1 of one lane: loads first, then the ray-value gathers
+template <typename WT, int R>
+__device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, const float *res, uint32_t off, int cnt,
+                                        float &num, float &den, bool &zero)
+{
+    uint32_t ry[R];
+    float wv[R], rv[R];
+#pragma unroll
+    for (int t = 0; t < R; t++) {
+        bool in = t < cnt;
+        uint32_t pos = off + (uint32_t)t * kSlice;
+        ry[t] = in ? __ldcs(cray + pos) : 0u;
+        wv[t] = in ? load_cs(cw, pos) : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg(res + ry[t]) : 0.f;
+#pragma unroll
+    for (int t = 0; t < R; t++) {
+        bool act = (wv[t] > 0.0f) && (rv[t] == rv[t]);
+        bool zr = act && (rv[t] == -INFINITY);
+        den += act ? wv[t] : 0.0f;
+        zero |= zr;
+        num += (act && !zr) ? wv[t] * rv[t] : 0.0f;
+    }
+}
+
+// Correction of slices wg, wg + W, ... of one representative (lane-ordered
+// cell-major store): each lane owns one cell; the next slice's descriptor
+// loads are issued before the current slice's gathers; the unrolled row loop
+// is sized per slice from lane 0's (widest) count.
+template <typename WT>
+__device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_off, long long base,
+                                           const uint32_t *__restrict__ slice_meta,
+                                           const uint16_t *__restrict__ lane_desc, const uint32_t *__restrict__ cray,
+                                           const WT *__restrict__ cw, const float *__restrict__ res,
+                                           float *__restrict__ f, const RingEntry *__restrict__ rt, int mG,
+                                           long long cps, long long n_slices, float lambda, long long wg, long long W,
+                                           int lane)
+{
+    long long sl = wg;
+    if (sl >= n_slices) return;
+    const uint32_t *cr = cray + base;
+    const WT *cwb = cw + base;
+    SliceDesc cur, nxt;
+    load_desc(cur, slice_off, base, slice_meta, lane_desc, sl, n_slices, lane);
+    for (; sl < n_slices; sl += W) {
+        int cnt = (int)(cur.d & 2047u);
+        int width = __shfl_sync(0xffffffffu, cnt, 0);
+        RingEntry re = rt[cell_ring(cur.m)];
+        int sec = cell_sector(cur.m) + (int)(cur.d >> 11);
+        int s2 = sec + mG * re.step;
+        s2 = s2 >= re.ng ? s2 - re.ng : s2;
+        long long cell = (long long)cell_slab(cur.m) * cps + re.head + s2;
+        float fv = cnt > 0 ? f[cell] : 0.0f;
+        uint32_t off = cur.off + lane;
+        load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
+        float num = 0.f, den = 0.f;
+        bool zero = false;
+        if (width <= 2) {
+            cm_rows<WT, 2>(cr, cwb, res, off, cnt, num, den, zero);
+        } else if (width <= 4) {
+            cm_rows<WT, 4>(cr, cwb, res, off, cnt, num, den, zero);
+        } else {
+            cm_rows<WT, 8>(cr, cwb, res, off, cnt, num, den, zero);
+            for (int t = 8; t < cnt; t++) {  // long columns (cells close to the source)
+                uint32_t pos = off + (uint32_t)t * kSlice;
+                float wt = load_cs(cwb, pos);
+                float r = __ldg(res + __ldcs(cr + pos));
+                bool act = (wt > 0.0f) && (r == r);
+                bool zr = act && (r == -INFINITY);
+                den += act ? wt : 0.0f;
+                zero |= zr;
+                num += (act && !zr) ? wt * r : 0.0f;
+            }
+        }
+        if (den > 0.0f) f[cell] = zero ? 0.0f : fv * expf(lambda * (num / den));
+        cur = nxt;
+    }
+}
+
+}  // namespace uspg

@@ -21,6 +21,7 @@
 // iterations -> views -> rays in order, prefetching the next row into
 // registers while the current ray is reduced and corrected.
 #include "internal.cuh"
+#include "device.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -49,161 +50,6 @@ StoreView store_view(const uspg_ctx *c, int rep)
     return v;
 }
 
-// ---- weight loads ------------------------------------------------------------
-
-__device__ __forceinline__ float4 load_w4(const float *w, long long q) { return *(const float4 *)(w + q); }
-__device__ __forceinline__ float4 load_w4(const __half *w, long long q)
-{
-    uint2 u = *(const uint2 *)(w + q);
-    float2 a = __half22float2(*(const __half2 *)&u.x), b = __half22float2(*(const __half2 *)&u.y);
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ float4 load_w4(const __nv_bfloat16 *w, long long q)
-{
-    uint2 u = *(const uint2 *)(w + q);
-    float2 a = __bfloat1622float2(*(const __nv_bfloat162 *)&u.x), b = __bfloat1622float2(*(const __nv_bfloat162 *)&u.y);
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ float load_w1(const float *w, long long q) { return w[q]; }
-__device__ __forceinline__ float load_w1(const __half *w, long long q) { return __half2float(w[q]); }
-__device__ __forceinline__ float load_w1(const __nv_bfloat16 *w, long long q) { return __bfloat162float(w[q]); }
-
-// rotated cell id of a stored entry; tab[ring] = {head, ng, q, 0}
-__device__ __forceinline__ long long rot_cell(const int4 *tab, long long cps, uint32_t pc)
-{
-    int4 t = tab[cell_ring(pc)];
-    int s = cell_sector(pc) + t.z;
-    s = s >= t.y ? s - t.y : s;
-    return (long long)cell_slab(pc) * cps + t.x + s;
-}
-
-__device__ __forceinline__ void fill_tab(int4 *tab, const RingEntry *rt, int n_rings, int mG, int tid, int nt)
-{
-    for (int i = tid; i < n_rings; i += nt) {
-        RingEntry e = rt[i];
-        tab[i] = make_int4(e.head, e.ng, mG * e.step, 0);
-    }
-}
-
-// ---- per-view forward ----------------------------------------------------------
-
-template <typename WT>
-__global__ void __launch_bounds__(256) k_forward(const long long *__restrict__ row_ptr, const uint32_t *__restrict__ idx,
-                                                 const WT *__restrict__ w, const float *__restrict__ f,
-                                                 const RingEntry *__restrict__ rt, int n_rings, int mG, long long cps,
-                                                 const float *__restrict__ proj, int n_rays, float w_scale,
-                                                 float *__restrict__ out_s, float *__restrict__ out_res)
-{
-    extern __shared__ int4 tab[];
-    fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
-    __syncthreads();
-    int ray = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    int lane = threadIdx.x & 31;
-    if (ray >= n_rays) return;
-    long long b = row_ptr[ray], e = row_ptr[ray + 1];
-    float acc = 0.0f;
-    // two 128-entry chunks per pass: all stream loads are issued before the
-    // eight dependent image gathers, so a typical row costs one round trip
-    // for the row and one for the gathers
-    for (long long q0 = b + 4 * lane; q0 < e; q0 += 256) {
-        long long q1 = q0 + 128;
-        bool two = q1 < e;
-        uint4 i0 = __ldg((const uint4 *)(idx + q0));
-        float4 w0 = load_w4(w, q0);
-        uint4 i1 = make_uint4(0, 0, 0, 0);
-        float4 w1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (two) {
-            i1 = __ldg((const uint4 *)(idx + q1));
-            w1 = load_w4(w, q1);
-        }
-        float g0 = __ldg(f + rot_cell(tab, cps, i0.x)), g1 = __ldg(f + rot_cell(tab, cps, i0.y));
-        float g2 = __ldg(f + rot_cell(tab, cps, i0.z)), g3 = __ldg(f + rot_cell(tab, cps, i0.w));
-        float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f;
-        if (two) {
-            h0 = __ldg(f + rot_cell(tab, cps, i1.x));
-            h1 = __ldg(f + rot_cell(tab, cps, i1.y));
-            h2 = __ldg(f + rot_cell(tab, cps, i1.z));
-            h3 = __ldg(f + rot_cell(tab, cps, i1.w));
-        }
-        acc = fmaf(w0.x, g0, acc);
-        acc = fmaf(w0.y, g1, acc);
-        acc = fmaf(w0.z, g2, acc);
-        acc = fmaf(w0.w, g3, acc);
-        acc = fmaf(w1.x, h0, acc);
-        acc = fmaf(w1.y, h1, acc);
-        acc = fmaf(w1.z, h2, acc);
-        acc = fmaf(w1.w, h3, acc);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-        float s = acc * w_scale;
-        if (out_s) out_s[ray] = s;
-        if (out_res) {
-            float res;
-            if (e == b || !(s > 0.0f)) {
-                res = __int_as_float(0x7fc00000);  // skip this ray
-            } else {
-                float p = proj[ray];
-                res = p > 0.0f ? logf(p / s) : -INFINITY;
-            }
-            out_res[ray] = res;
-        }
-    }
-}
-
-// ---- per-view correction (cell-major) -----------------------------------------
-
-template <typename WT>
-__global__ void __launch_bounds__(256) k_backward(const long long *__restrict__ slice_off,
-                                                  const uint32_t *__restrict__ slice_meta,
-                                                  const int *__restrict__ slice_width, const uint32_t *__restrict__ sray,
-                                                  const WT *__restrict__ sw, const float *__restrict__ res,
-                                                  float *__restrict__ f, const RingEntry *__restrict__ rt, int mG,
-                                                  long long cps, long long n_slices, float lambda)
-{
-    long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (sl >= n_slices) return;
-    uint32_t meta = slice_meta[sl];
-    int width = slice_width[sl];
-    long long off = slice_off[sl] + lane;
-    int ring = cell_ring(meta);
-    RingEntry re = rt[ring];
-    int sec = cell_sector(meta) + lane;
-    bool own = sec < re.ng;
-    int s2 = sec + mG * re.step;
-    s2 = s2 >= re.ng ? s2 - re.ng : s2;
-    long long cell = (long long)cell_slab(meta) * cps + re.head + s2;
-    float fv = own ? f[cell] : 0.0f;  // issued early, used at the end
-    float num = 0.0f, den = 0.0f;
-    bool zero = false;
-    // four entries per pass: stream loads first, then the ray gathers
-    for (int t = 0; t < width; t += 4) {
-        uint32_t ry[4];
-        float wv[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            long long pos = off + (long long)(t + u) * kSlice;
-            bool in = t + u < width;
-            ry[u] = in ? __ldg(sray + pos) : 0u;
-            wv[u] = in ? load_w1(sw, pos) : 0.0f;
-        }
-        float r[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) r[u] = __ldg(res + ry[u]);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            bool act = (wv[u] > 0.0f) && (r[u] == r[u]);
-            bool zr = act && (r[u] == -INFINITY);
-            den += act ? wv[u] : 0.0f;
-            zero |= zr;
-            num += (act && !zr) ? wv[u] * r[u] : 0.0f;
-        }
-    }
-    if (own && den > 0.0f) f[cell] = zero ? 0.0f : fv * expf(lambda * (num / den));
-}
-
 // ---- per-view forward: entry-parallel ------------------------------------------
 //
 // Rows of the ray-major store start and end on multiples of kRowPad (= 8)
@@ -215,71 +61,6 @@ __global__ void __launch_bounds__(256) k_backward(const long long *__restrict__ 
 // read with evict-first loads (__ldcs) so the image stays in L2 across views.
 // k_forward_finalize turns the sums into ln(P/Pbar) and clears sacc.
 
-__device__ __forceinline__ void load_w8(const float *w, long long q, float o[8])
-{
-    float4 a = __ldcs((const float4 *)(w + q)), b = __ldcs((const float4 *)(w + q + 4));
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
-}
-__device__ __forceinline__ void load_w8(const __half *w, long long q, float o[8])
-{
-    uint4 u = __ldcs((const uint4 *)(w + q));
-    const __half2 *h = (const __half2 *)&u;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        float2 v = __half22float2(h[i]);
-        o[2 * i] = v.x;
-        o[2 * i + 1] = v.y;
-    }
-}
-__device__ __forceinline__ void load_w8(const __nv_bfloat16 *w, long long q, float o[8])
-{
-    uint4 u = __ldcs((const uint4 *)(w + q));
-    const __nv_bfloat162 *h = (const __nv_bfloat162 *)&u;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        float2 v = __bfloat1622float2(h[i]);
-        o[2 * i] = v.x;
-        o[2 * i + 1] = v.y;
-    }
-}
-__device__ __forceinline__ float load_cs(const float *w, long long q) { return __ldcs(w + q); }
-__device__ __forceinline__ float load_cs(const __half *w, long long q)
-{
-    return __half2float(__ushort_as_half(__ldcs((const unsigned short *)(w + q))));
-}
-__device__ __forceinline__ float load_cs(const __nv_bfloat16 *w, long long q)
-{
-    return __bfloat162float(__ushort_as_bfloat16(__ldcs((const unsigned short *)(w + q))));
-}
-
-template <typename WT>
-struct Group8 {
-    uint32_t c[8];
-    float w[8];
-    uint32_t ray;
-};
-
-template <typename WT>
-__device__ __forceinline__ void load_group(Group8<WT> &G, const uint32_t *idx, const WT *w, const uint32_t *grp_ray,
-                                           long long g, bool valid)
-{
-    if (valid) {
-        long long q = g * kRowPad;
-        uint4 ia = __ldcs((const uint4 *)(idx + q)), ib = __ldcs((const uint4 *)(idx + q + 4));
-        load_w8(w, q, G.w);
-        G.ray = __ldcs(grp_ray + g);
-        G.c[0] = ia.x; G.c[1] = ia.y; G.c[2] = ia.z; G.c[3] = ia.w;
-        G.c[4] = ib.x; G.c[5] = ib.y; G.c[6] = ib.z; G.c[7] = ib.w;
-    } else {
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            G.c[i] = 0;
-            G.w[i] = 0.0f;
-        }
-        G.ray = 0xffffffffu;
-    }
-}
-
 template <typename WT>
 __global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict__ idx, const WT *__restrict__ w,
                                                       const uint32_t *__restrict__ grp_ray, long long g0,
@@ -290,56 +71,16 @@ __global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict
     extern __shared__ int4 tab[];
     fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long step = (((long long)gridDim.x * blockDim.x) >> 5) * 32;
-    long long base = gw * 32;
-    if (base >= n_groups) return;
-    // two register buffers: the next chunk's stream loads are in flight while
-    // the current chunk's gathers wait
-    Group8<WT> cur, nxt;
-    load_group(cur, idx, w, grp_ray, g0 + base + lane, base + lane < n_groups);
-    for (; base < n_groups; base += step) {
-        long long nb = base + step;
-        load_group(nxt, idx, w, grp_ray, g0 + nb + lane, nb + lane < n_groups);
-        float gv[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) gv[i] = cur.w[i] != 0.0f ? __ldg(f + rot_cell(tab, cps, cur.c[i])) : 0.0f;
-        float acc = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 8; i++) acc = fmaf(cur.w[i], gv[i], acc);
-        uint32_t ray = cur.ray;
-        // segmented sum over lanes of the same ray (they are consecutive)
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            float v2 = __shfl_down_sync(0xffffffffu, acc, o);
-            uint32_t r2 = __shfl_down_sync(0xffffffffu, ray, o);
-            if (lane + o < 32 && r2 == ray) acc += v2;
-        }
-        uint32_t rprev = __shfl_up_sync(0xffffffffu, ray, 1);
-        if (ray != 0xffffffffu && (lane == 0 || rprev != ray)) atomicAdd(&sacc[ray], acc);
-        cur = nxt;
-    }
+    fwd_groups<WT>(idx, w, grp_ray, g0, n_groups, f, tab, cps, sacc,
+                   ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((long long)gridDim.x * blockDim.x) >> 5,
+                   threadIdx.x & 31);
 }
 
 __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__restrict__ proj, int n_rays, float w_scale,
                                    float *__restrict__ out_s, float *__restrict__ out_res)
 {
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray >= n_rays) return;
-    float sv = sacc[ray] * w_scale;
-    sacc[ray] = 0.0f;
-    if (out_s) out_s[ray] = sv;
-    if (out_res) {
-        float res;
-        if (!(sv > 0.0f)) {
-            res = __int_as_float(0x7fc00000);  // empty row or zero sum: skip this ray
-        } else {
-            float p = proj[ray];
-            res = p > 0.0f ? logf(p / sv) : -INFINITY;
-        }
-        out_res[ray] = res;
-    }
+    if (ray < n_rays) finalize_ray(sacc, proj, ray, w_scale, out_s, out_res);
 }
 
 // ---- per-view correction: lane-ordered cell-major store --------------------------
@@ -349,51 +90,6 @@ __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__rest
 // slice_off + 32 t + l for t < n.  All stream loads of the warp's slices are
 // issued before the ray-value gathers, and the image value of each cell is
 // fetched first so that its latency overlaps the stream.
-struct SliceDesc {
-    uint32_t d, m, off;
-};
-
-__device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_off, long long base,
-                                          const uint32_t *slice_meta, const uint16_t *lane_desc, long long sl,
-                                          long long n_slices, int lane)
-{
-    if (sl < n_slices) {
-        D.d = lane_desc[sl * 32 + lane];
-        D.m = slice_meta[sl];
-        D.off = (uint32_t)(slice_off[sl] - base);
-    } else {
-        D.d = 0;
-        D.m = 0;
-        D.off = 0;
-    }
-}
-
-// rows 0..R-1 of one lane: loads first, then the ray-value gathers
-template <typename WT, int R>
-__device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, const float *res, uint32_t off, int cnt,
-                                        float &num, float &den, bool &zero)
-{
-    uint32_t ry[R];
-    float wv[R], rv[R];
-#pragma unroll
-    for (int t = 0; t < R; t++) {
-        bool in = t < cnt;
-        uint32_t pos = off + (uint32_t)t * kSlice;
-        ry[t] = in ? __ldcs(cray + pos) : 0u;
-        wv[t] = in ? load_cs(cw, pos) : 0.0f;
-    }
-#pragma unroll
-    for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg(res + ry[t]) : 0.f;
-#pragma unroll
-    for (int t = 0; t < R; t++) {
-        bool act = (wv[t] > 0.0f) && (rv[t] == rv[t]);
-        bool zr = act && (rv[t] == -INFINITY);
-        den += act ? wv[t] : 0.0f;
-        zero |= zr;
-        num += (act && !zr) ? wv[t] * rv[t] : 0.0f;
-    }
-}
-
 // Persistent warps, one slice per step: the next slice's descriptor loads are
 // issued before the current slice's gathers.  The slice's widest column is
 // lane 0's (lanes are ordered by count), so the unrolled row loop is sized
@@ -407,48 +103,9 @@ __global__ void __launch_bounds__(256) k_backward_sell(const long long *__restri
                                                        const RingEntry *__restrict__ rt, int mG, long long cps,
                                                        long long n_slices, float lambda)
 {
-    const int lane = threadIdx.x & 31;
-    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long W = ((long long)gridDim.x * blockDim.x) >> 5;
-    long long sl = wg;
-    if (sl >= n_slices) return;
-    const uint32_t *cr = cray + base;
-    const WT *cwb = cw + base;
-    SliceDesc cur, nxt;
-    load_desc(cur, slice_off, base, slice_meta, lane_desc, sl, n_slices, lane);
-    for (; sl < n_slices; sl += W) {
-        int cnt = (int)(cur.d & 2047u);
-        int width = __shfl_sync(0xffffffffu, cnt, 0);
-        RingEntry re = rt[cell_ring(cur.m)];
-        int sec = cell_sector(cur.m) + (int)(cur.d >> 11);
-        int s2 = sec + mG * re.step;
-        s2 = s2 >= re.ng ? s2 - re.ng : s2;
-        long long cell = (long long)cell_slab(cur.m) * cps + re.head + s2;
-        float fv = cnt > 0 ? f[cell] : 0.0f;
-        uint32_t off = cur.off + lane;
-        load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
-        float num = 0.f, den = 0.f;
-        bool zero = false;
-        if (width <= 2) {
-            cm_rows<WT, 2>(cr, cwb, res, off, cnt, num, den, zero);
-        } else if (width <= 4) {
-            cm_rows<WT, 4>(cr, cwb, res, off, cnt, num, den, zero);
-        } else {
-            cm_rows<WT, 8>(cr, cwb, res, off, cnt, num, den, zero);
-            for (int t = 8; t < cnt; t++) {  // long columns (cells close to the source)
-                uint32_t pos = off + (uint32_t)t * kSlice;
-                float wt = load_cs(cwb, pos);
-                float r = __ldg(res + __ldcs(cr + pos));
-                bool act = (wt > 0.0f) && (r == r);
-                bool zr = act && (r == -INFINITY);
-                den += act ? wt : 0.0f;
-                zero |= zr;
-                num += (act && !zr) ? wt * r : 0.0f;
-            }
-        }
-        if (den > 0.0f) f[cell] = zero ? 0.0f : fv * expf(lambda * (num / den));
-        cur = nxt;
-    }
+    bwd_slices<WT>(slice_off, base, slice_meta, lane_desc, cray, cw, res, f, rt, mG, cps, n_slices, lambda,
+                   ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((long long)gridDim.x * blockDim.x) >> 5,
+                   threadIdx.x & 31);
 }
 
 template <typename WT>

@@ -89,6 +89,10 @@ def lib():
             "uspg_mart_kernel_times": ([V, P(MartOpts), V, V, I32, P(I32), V], I32),
             "uspg_autotune": ([V, V, V], I32),
             "uspg_forward_project_noalloc": ([V, I32, V, V, V], I32),
+            "uspg_batch_create": ([V, I32, P(MartOpts), V, P(V)], I32),
+            "uspg_batch_run": ([V, V], I32),
+            "uspg_batch_info": ([V, P(I64), P(I64), P(I64)], I32),
+            "uspg_batch_destroy": ([V], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -260,3 +264,25 @@ def uspg_forward_project_noalloc(ctx, view: int, f, out, stream=None):
     (accumulator in the library's static device array); ``f`` and ``out`` are
     device tensors."""
     _check(lib().uspg_forward_project_noalloc(ctx, view, _ptr(f), _ptr(out), _stream(stream)), ctx)
+
+
+def uspg_batch_create(ctxs, opts: MartOpts, stream=None):
+    """Batched per-view MART over several contexts (one CUDA graph)."""
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    h = C.c_void_p()
+    _check(lib().uspg_batch_create(arr, len(ctxs), C.byref(opts), _stream(stream), C.byref(h)), None)
+    return h.value
+
+
+def uspg_batch_run(batch, stream=None):
+    _check(lib().uspg_batch_run(batch, _stream(stream)), None)
+
+
+def uspg_batch_info(batch) -> dict:
+    u, k, s = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _check(lib().uspg_batch_info(batch, C.byref(u), C.byref(k), C.byref(s)), None)
+    return {"updates_per_run": u.value, "kernel_nodes": k.value, "steps": s.value}
+
+
+def uspg_batch_destroy(batch):
+    lib().uspg_batch_destroy(batch)

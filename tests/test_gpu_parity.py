@@ -329,3 +329,43 @@ def test_reduced_precision_mart_error(torch_cuda):
     assert err["f32"] < TOL_IMG
     assert err["f16"] < 2e-3
     assert err["bf16"] < 1e-2
+
+
+# ---------------------------------------------------------------- batched ---
+
+def test_batched_instances_match_single_runs(torch_cuda):
+    """Contexts of different grids, view counts and detectors advanced together
+    in one graph give each context the image its own uspg_mart gives."""
+    from paper_2208_12964_gb300 import uspg
+
+    specs = [synth.parallel_workload(12, 18, 25, seed=31, iterations=3, lam=0.3),
+             synth.parallel_workload(20, 36, 41, seed=32, iterations=3, lam=0.3),
+             synth.parallel_workload(7, 10, 15, seed=33, iterations=3, lam=0.3),
+             synth.cone_workload(10, 6, 12, 16, iterations=3, lam=0.2, seed=34),
+             synth.cone_workload(14, 10, 18, 24, iterations=3, lam=0.2, seed=35)]
+    gs, projs, refs = [], [], []
+    for sp in specs:
+        g = Gpu(sp).build()
+        p = synth.projections(sp)
+        n = g.stats()["n_cells"]
+        refs.append(_run_mart(g, p, np.ones(n), 3, 0.3 if sp["geometry"] == 0 else 0.2, 1))
+        gs.append(g)
+        projs.append(p)
+    # lambda differs between the two families: run one batch per family
+    for fam, lam in ((0, 0.3), (1, 0.2)):
+        sel = [i for i, sp in enumerate(specs) if sp["geometry"] == fam]
+        for i in sel:
+            uspg.uspg_fill_image(gs[i].ctx, 1.0)
+        opts, _ = uspg.mart_opts(3, lam, uspg.PER_VIEW)
+        b = uspg.uspg_batch_create([gs[i].ctx for i in sel], opts)
+        try:
+            info = uspg.uspg_batch_info(b)
+            assert info["steps"] == 3 * max(specs[i]["n_views"] for i in sel)
+            uspg.uspg_batch_run(b)
+            torch_cuda.cuda.synchronize()
+        finally:
+            uspg.uspg_batch_destroy(b)
+        for i in sel:
+            got = np.zeros(gs[i].stats()["n_cells"], np.float32)
+            uspg.uspg_get_image(gs[i].ctx, got, False)
+            assert rel_l2(got, refs[i]) < 1e-5, i
