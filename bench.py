@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--coeff-dtype", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serve-mixed: mean requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serve-mixed: arrival window")
+    ap.add_argument("--serve-active", type=int, default=16, help="serve-mixed: jobs resident at once")
     return ap.parse_args()
 
 
@@ -417,6 +420,164 @@ def run_batched(args, rank, world, local):
     return 0
 
 
+SERVE_2D = [(R, V) for R in (64, 128, 256, 512) for V in (18, 36, 90, 180)]
+SERVE_3D = [(64, 45, 128), (128, 90, 256), (256, 180, 512)]
+
+
+def serve_trace(rate: float, seconds: float, seed: int = 5):
+    """Seeded Poisson request stream of the mixed serving workload: exponential
+    gaps of mean 1/rate; 80% 2D parallel-beam jobs (rings from {64, 128, 256,
+    512}, views from {18, 36, 90, 180} over a half turn, 2R+1 bins, 10 per-view
+    iterations, lambda 0.2) and 20% 3D cone-beam jobs (rings = slabs, views,
+    detector) in {(64, 45, 128^2), (128, 90, 256^2), (256, 180, 512^2)}, 5
+    iterations, lambda 0.1.  Returns [(arrival seconds, geometry key)]."""
+    import math
+
+    from paper_2208_12964_gb300 import synth
+
+    g = synth.Stream(seed)
+    t, out = 0.0, []
+    while True:
+        u, k, a = g.u(3)
+        t += -math.log(1.0 - u) / rate
+        if t >= seconds:
+            return out
+        if k < 0.8:
+            R, V = SERVE_2D[min(int(a * len(SERVE_2D)), len(SERVE_2D) - 1)]
+            out.append((t, ("2d", R, V)))
+        else:
+            out.append((t, ("3d",) + SERVE_3D[min(int(a * len(SERVE_3D)), len(SERVE_3D) - 1)]))
+
+
+def serve_spec(key):
+    from paper_2208_12964_gb300 import synth
+
+    if key[0] == "2d":
+        R, V = key[1:]
+        return synth.parallel_workload(R, V, 2 * R + 1, seed=200 + R + V, iterations=10, lam=0.2)
+    R, V, D = key[1:]
+    return synth.cone_workload(R, R, V, D, iterations=5, lam=0.1, seed=300 + R, noise=False)
+
+
+def run_serving(args, rank, world, local):
+    """The request loop of the library (uspg_server_*) under a Poisson stream:
+    each request is submitted at its arrival time with its projections read in
+    place from page-locked host memory; the result image comes back to host
+    memory.  The same trace is served with FP16 and with FP32 coefficients.
+    Before the timed trace one request per geometry runs untimed, so every
+    store is resident (the steady state of a server that has seen its
+    protocols); the images of those requests give the FP16-vs-FP32 error."""
+    import torch
+
+    from paper_2208_12964_gb300 import synth, uspg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    trace = serve_trace(args.serve_rate, args.serve_seconds)
+    keys = sorted({k for _, k in trace})
+    specs = {k: serve_spec(k) for k in keys}
+    proj = {k: torch.from_numpy(synth.projections(specs[k])).pin_memory() for k in keys}
+    free, _total = torch.cuda.mem_get_info(dev)
+    budget = int(free * 0.85)
+    runs, images = {}, {}
+    for name, dt in (("f16", uspg.F16), ("f32", uspg.F32)):
+        srv = uspg.uspg_server_create(budget, args.serve_active, 1)
+        try:
+            warm = {k: uspg.uspg_server_submit(srv, specs[k], proj[k],
+                                               uspg.mart_opts(specs[k]["iterations"], specs[k]["lam"],
+                                                              uspg.PER_VIEW)[0], dt, borrow=True) for k in keys}
+            uspg.uspg_server_drain(srv, 1800.0)
+            for k, jid in warm.items():
+                img = np.zeros(_n_cells(specs[k]), np.float32)
+                r = uspg.uspg_server_poll(srv, jid, img)
+                if r["status"] != uspg.OK:
+                    raise RuntimeError(f"warm-up job {k} failed: {r['message']}")
+                images.setdefault(k, {})[name] = img
+            opts = {k: uspg.mart_opts(specs[k]["iterations"], specs[k]["lam"], uspg.PER_VIEW)[0] for k in keys}
+            torch.cuda.synchronize(dev)
+            launches0 = uspg.uspg_kernel_launches()
+            results, pending = [], []
+            with ClockSampler(local) as clk:
+                t0 = time.perf_counter()
+                for t_arr, k in trace:
+                    while True:
+                        now = time.perf_counter() - t0
+                        if now >= t_arr:
+                            break
+                        if pending:
+                            pending = _serve_poll(uspg, srv, pending, results)
+                        time.sleep(min(2e-4, max(t_arr - now, 0.0)))
+                    pending.append(uspg.uspg_server_submit(srv, specs[k], proj[k], opts[k], dt, borrow=True))
+                t_sub = time.perf_counter() - t0
+                uspg.uspg_server_drain(srv, 1800.0)
+                wall = time.perf_counter() - t0
+                pending = _serve_poll(uspg, srv, pending, results)
+            launches = uspg.uspg_kernel_launches() - launches0
+            st = uspg.uspg_server_stats(srv)
+        finally:
+            uspg.uspg_server_destroy(srv)
+        bad = [r for r in results if r["status"] != uspg.OK]
+        if bad or pending:
+            raise RuntimeError(f"{len(bad)} served jobs failed, {len(pending)} not collected: "
+                               f"{bad[0]['message'] if bad else ''}")
+        lat = np.array([r["latency_s"] for r in results]) * 1e3
+        upd = sum(r["updates"] for r in results)
+        runs[name] = {"value": upd / wall, "jobs_per_s": len(results) / wall, "wall_s": wall,
+                      "submit_window_s": t_sub, "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                      "max_ms": float(lat.max()), "queue_p50_ms": float(np.percentile(
+                          [r["queue_s"] * 1e3 for r in results], 50)),
+                      "store_reuses": st["store_reuses"], "peak_device_bytes": st["peak_device_bytes"],
+                      "gpu_launches": int(launches), "clocks": clk.summary()}
+    errs = []
+    for k in keys:
+        a, b = images[k]["f16"].astype(np.float64), images[k]["f32"].astype(np.float64)
+        errs.append(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)))
+    f16, f32 = runs["f16"], runs["f32"]
+    n2 = sum(1 for _, k in trace if k[0] == "2d")
+    line = {"metric": METRIC + " (served)", "value": f16["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": len(trace), "warmup": len(keys), "ms_per_step": f16["wall_s"] * 1e3 / len(trace),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16 coefficients, f32 image and accumulation", "data": "synthetic",
+            "config": {"workload": "serve-mixed", "offered_rate_per_s": args.serve_rate,
+                       "arrival_window_s": args.serve_seconds, "requests": len(trace), "requests_2d": n2,
+                       "requests_3d": len(trace) - n2, "geometries": len(keys), "max_active": args.serve_active,
+                       "chunk": "1 sweep", "device_budget_bytes": budget,
+                       "step": "one request (value = updates of all requests / wall time from first "
+                               "arrival to last result)",
+                       "l2": "inputs of the 3D jobs exceed L2; no flush between requests"},
+            "latency_ms": {"p50": f16["p50_ms"], "p99": f16["p99_ms"], "mean": f16["mean_ms"], "max": f16["max_ms"],
+                           "queue_p50": f16["queue_p50_ms"]},
+            "jobs_per_s": f16["jobs_per_s"], "wall_s": f16["wall_s"], "store_reuses": f16["store_reuses"],
+            "peak_device_bytes": f16["peak_device_bytes"],
+            "fp32_coefficients": {k_: f32[k_] for k_ in ("value", "jobs_per_s", "p50_ms", "p99_ms", "mean_ms",
+                                                         "max_ms", "wall_s")},
+            "image_rel_l2_f16_vs_f32": {"median": float(np.median(errs)), "max": float(max(errs))},
+            "e2e": {"value": f16["value"], "unit": UNIT, "how": "host projections in, host image out, per request",
+                    "h2d_bytes_per_step": int(np.mean([proj[k].numel() * 4 for _, k in trace])),
+                    "d2h_bytes_per_step": int(np.mean([_n_cells(specs[k]) * 4 for _, k in trace]))},
+            "gpu_launches": f16["gpu_launches"], "clocks": f16["clocks"]}
+    print(json.dumps(line))
+    return 0
+
+
+def _n_cells(spec):
+    R = spec["n_rings"]
+    per_slab = 3 * R * (R + 1)  # 6n sectors per ring
+    return per_slab * (spec["n_slabs"] if spec["geometry"] == 1 else 1)
+
+
+def _serve_poll(uspg, srv, pending, results):
+    left = []
+    for jid in pending:
+        r = uspg.uspg_server_poll(srv, jid)
+        if r is None:
+            left.append(jid)
+        else:
+            results.append(r)
+    return left
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -424,6 +585,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch-2d-64":
         return run_batched(args, rank, world, local)
+    if args.workload == "serve-mixed":
+        return run_serving(args, rank, world, local)
     info = run_ours(args, rank, world, local)
     if rank != 0:
         return 0

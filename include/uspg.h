@@ -221,6 +221,92 @@ uspg_status uspg_batch_run(uspg_batch *batch, uspg_stream stream);
 uspg_status uspg_batch_info(const uspg_batch *batch, int64_t *updates_per_run, int64_t *kernel_nodes, int64_t *steps);
 void uspg_batch_destroy(uspg_batch *batch);
 
+/* --- reconstruction server ------------------------------------------------------ */
+
+/* A request loop that serves many reconstructions (Sec. III.D MART jobs of any
+ * grid and scan) concurrently on one GPU.  One scheduler thread owns all
+ * device work:
+ *  - admission: a queued job starts when fewer than max_active jobs run and
+ *    its device footprint fits device_budget (bytes) next to the running ones;
+ *  - store sharing: the first job of a geometry (grid, scan, coefficient model
+ *    and dtype) builds its coefficients; every later or concurrent job of that
+ *    geometry reads the same store through a context of its own (image,
+ *    projections, scratch), and finished jobs' contexts are pooled for reuse;
+ *    a geometry with no running job is freed, least recently used first, when
+ *    an admission needs its memory;
+ *  - continuous batching: each running job has its own stream and advances by
+ *    chunks of chunk_sweeps sweeps (PER_VIEW; one sweep = every view once, one
+ *    CUDA-graph launch); every pass of the scheduler issues the next chunk of
+ *    each job whose previous chunk has finished, so jobs overlap on the device
+ *    and a new job starts without waiting for the running ones to end;
+ *  - preparation: a second library thread builds the coefficients of a job
+ *    whose geometry is not resident and uploads its projections, so neither
+ *    stalls the running jobs.
+ * Each job computes exactly what uspg_mart computes for it alone (the same
+ * kernels on the same store, view order 0..p-1), up to the order of the
+ * forward kernel's floating-point atomic additions.  Thread safe: submit,
+ * poll and stats may be called from any host thread.  The server uses the
+ * device current when it is created. */
+typedef struct uspg_server uspg_server;
+
+typedef struct {
+    uspg_grid_desc grid;      /* grid.sectors (CUSTOM) is copied at submit */
+    uspg_scan_desc scan;
+    uspg_coeff_opts coeff;
+    uspg_mart_opts mart;      /* view_order, view_steps and stop_tol are ignored for PER_VIEW;
+                                 PER_VIEW takes the POWER rule */
+    const float *projections; /* host float32 [views][rays]: copied at submit, or read in place
+                                 with USPG_JOB_BORROW_PROJECTIONS */
+    float f0;                 /* initial value of every cell */
+    int32_t flags;            /* 0 or USPG_JOB_BORROW_PROJECTIONS */
+} uspg_job;
+
+/* The server reads the job's projections from the caller's buffer when it
+ * prepares the job instead of copying them at submit; the caller keeps the
+ * buffer alive and unchanged until uspg_server_poll has returned the job's
+ * result.  Page-locked buffers upload fastest. */
+#define USPG_JOB_BORROW_PROJECTIONS 1
+
+typedef struct {
+    uspg_status status;   /* the job's own outcome (ENOMEM: its store exceeds the budget) */
+    int32_t reused_store; /* 1 if another job of the same geometry built the coefficients */
+    int64_t n_cells;      /* floats written to image */
+    int64_t updates;      /* ray-cell updates the job ran (iterations x nonzeros over all views) */
+    double queue_s;       /* submit -> start */
+    double run_s;         /* start -> image on host (includes any coefficient build) */
+    double latency_s;     /* submit -> image on host */
+    char message[200];    /* why a failed job failed (empty on success) */
+} uspg_job_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, queued, active;
+    int64_t store_reuses;                   /* admissions that read a store another job built */
+    int64_t device_bytes, peak_device_bytes; /* held by running and idle contexts */
+    double p50_s, p99_s, mean_s;            /* latency (submit -> result) of completed jobs */
+    double jobs_per_s, updates_per_s;       /* completed work / time since the first submit */
+} uspg_server_report;
+
+/* Starts the scheduler and preparer threads.  EINVAL for a zero budget,
+ * max_active < 1 or chunk_sweeps < 1. */
+uspg_status uspg_server_create(size_t device_budget, int32_t max_active, int32_t chunk_sweeps, uspg_server **out);
+/* Copies the job (projections included) into the queue and returns its id.
+ * EINVAL for a malformed job (NULL projections, iterations < 1, lambda
+ * outside (0, 2), bad sizes); EUNSUPPORTED for PER_VIEW with LINEAR_EQ18.
+ * Geometry errors surface later as the job's status. */
+uspg_status uspg_server_submit(uspg_server *server, const uspg_job *job, uint64_t *id);
+/* ENOTREADY while job `id` is queued or running.  Once it has ended: fills
+ * *result (optional), copies the image to host `image` (optional, float32
+ * [n_cells]; nothing is copied for a failed job), forgets the job and
+ * returns OK -- the job's own outcome is result->status.  EINVAL for an
+ * unknown id. */
+uspg_status uspg_server_poll(uspg_server *server, uint64_t id, float *image, uspg_job_result *result);
+/* Blocks until every submitted job has ended, or ETIMEOUT after timeout_s. */
+uspg_status uspg_server_drain(uspg_server *server, double timeout_s);
+uspg_status uspg_server_stats(uspg_server *server, uspg_server_report *out);
+/* Lets running jobs finish, drops queued ones, frees every context and the
+ * jobs never polled, and joins the scheduler. */
+void uspg_server_destroy(uspg_server *server);
+
 /* --- display (Sec. II.B) ------------------------------------------------------- */
 
 /* USPG -> Cartesian.  POINT: an nx x ny image over [-R, R]^2 per slab, each

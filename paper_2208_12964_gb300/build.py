@@ -26,6 +26,7 @@ UNITS = {
     "mart.cu": [],
     "resample.cu": ["-fmad=false"],
     "batch.cu": [],
+    "server.cu": [],
 }
 
 

@@ -87,10 +87,43 @@ static void free_store(uspg_ctx *c)
     c->graphs.clear();
 }
 
+// reconstruction state: image, projections, per-ray scratch, flags
+static uspg_status alloc_state(uspg_ctx *c)
+{
+    if (c->d_f) return USPG_OK;
+    USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * c->n_cells));
+    USPG_CUDA(c, cudaMalloc(&c->d_proj, sizeof(float) * (long long)c->scan.n_views * c->n_rays));
+    USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * c->n_rays));
+    USPG_CUDA(c, cudaMalloc(&c->d_sacc, sizeof(float) * c->n_rays));
+    USPG_CUDA(c, cudaMemset(c->d_sacc, 0, sizeof(float) * c->n_rays));
+    USPG_CUDA(c, cudaMalloc(&c->d_status, sizeof(int)));
+    USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    USPG_CUDA(c, cudaMalloc(&c->d_sweeps, sizeof(int)));
+    USPG_CUDA(c, cudaMemset(c->d_sweeps, 0, sizeof(int)));
+    USPG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    return USPG_OK;
+}
+
+static void free_state(uspg_ctx *c)
+{
+    for (auto &kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    c->graphs.clear();
+    cudaFree(c->d_f);
+    cudaFree(c->d_proj);
+    cudaFree(c->d_res);
+    cudaFree(c->d_sacc);
+    cudaFree(c->d_status);
+    cudaFree(c->d_sweeps);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
 // device buffers that do not depend on the store
 static uspg_status ensure_state(uspg_ctx *c)
 {
-    if (c->d_ring) return USPG_OK;
+    if (c->d_ring) return alloc_state(c);
     std::vector<RingEntry> rt(c->n_rings);
     int chunk = 0;
     for (int i = 0; i < c->n_rings; i++) {
@@ -104,17 +137,49 @@ static uspg_status ensure_state(uspg_ctx *c)
     c->slices_per_rep = (long long)chunk * (c->scan.geometry == USPG_CONE_3D ? c->n_slabs : 1);
     USPG_CUDA(c, cudaMalloc(&c->d_ring, sizeof(RingEntry) * c->n_rings));
     USPG_CUDA(c, cudaMemcpy(c->d_ring, rt.data(), sizeof(RingEntry) * c->n_rings, cudaMemcpyHostToDevice));
-    USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * c->n_cells));
-    USPG_CUDA(c, cudaMalloc(&c->d_proj, sizeof(float) * (long long)c->scan.n_views * c->n_rays));
-    USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * c->n_rays));
-    USPG_CUDA(c, cudaMalloc(&c->d_sacc, sizeof(float) * c->n_rays));
-    USPG_CUDA(c, cudaMemset(c->d_sacc, 0, sizeof(float) * c->n_rays));
-    USPG_CUDA(c, cudaMalloc(&c->d_status, sizeof(int)));
-    USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
-    USPG_CUDA(c, cudaMalloc(&c->d_sweeps, sizeof(int)));
-    USPG_CUDA(c, cudaMemset(c->d_sweeps, 0, sizeof(int)));
-    USPG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    return alloc_state(c);
+}
+
+uspg_status ctx_share_store(const uspg_ctx *src, uspg_ctx **out)
+{
+    *out = nullptr;
+    if (!src->built || src->store_src) return fail(nullptr, USPG_EINVAL, "share: source store not built or shared");
+    uspg_ctx *c = new uspg_ctx(*src);  // host tables and store pointers
+    c->store_src = src;
+    c->graphs.clear();  // graphs capture the source's own image and scratch
+    c->err.clear();
+    c->have_proj = false;
+    c->d_f = c->d_proj = c->d_res = c->d_sacc = nullptr;
+    c->d_status = c->d_sweeps = nullptr;
+    c->cap_stream = nullptr;
+    c->d_counts = c->d_rep_view = c->d_cell_cnt = c->d_cell_fill = nullptr;  // generator scratch: never used
+    c->d_rel = c->d_stats = nullptr;
+    c->d_w64 = nullptr;
+    uspg_status st = alloc_state(c);
+    if (st) {
+        g_create_err = c->err;
+        free_state(c);
+        delete c;
+        return st;
+    }
+    *out = c;
     return USPG_OK;
+}
+
+long long ctx_device_bytes(const uspg_ctx *c)
+{
+    int wb = c->dtype == USPG_F32 ? 4 : 2;
+    long long rows = (long long)c->n_reps * c->n_rays, slices = c->slices_per_rep * c->n_reps;
+    long long b = 4LL * c->n_cells + 4LL * c->scan.n_views * c->n_rays + 8LL * c->n_rays;  // image, projections, scratch
+    if (c->store_src) return b;
+    b += (long long)sizeof(RingEntry) * c->n_rings + 24LL * c->cells_per_slab;  // ring table, boundaries
+    if (c->d_row_ptr) {
+        b += 8LL * (rows + 1) * 2 + 4LL * rows + 4LL * (rows + 1);                       // row pointers, counts, max
+        b += (long long)c->cap_idx * (4 + wb + 8) + 4LL * c->cap_grp;                    // rows, FP64 weights, groups
+        b += (long long)c->cap_sell * (4 + wb) + (long long)c->cap_cm * (4 + wb);        // padded and lane-ordered
+        b += slices * (8 + 4 + 4 + 64) + 8LL * c->n_cells + 8LL * (c->slices_per_rep + 1);  // slices, cell scratch
+    }
+    return b;
 }
 
 }  // namespace uspg
@@ -250,17 +315,13 @@ void uspg_destroy(uspg_ctx *c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
-    free_store(c);
-    cudaFree(c->d_ring);
-    cudaFree(c->d_bdir);
-    cudaFree(c->d_bdirf);
-    cudaFree(c->d_f);
-    cudaFree(c->d_proj);
-    cudaFree(c->d_res);
-    cudaFree(c->d_sacc);
-    cudaFree(c->d_status);
-    cudaFree(c->d_sweeps);
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    free_state(c);
+    if (!c->store_src) {
+        free_store(c);
+        cudaFree(c->d_ring);
+        cudaFree(c->d_bdir);
+        cudaFree(c->d_bdirf);
+    }
     delete c;
 }
 
@@ -287,6 +348,7 @@ uspg_status uspg_sync(uspg_ctx *c, uspg_stream stream)
 uspg_status uspg_build_coeffs(uspg_ctx *c, uspg_stream stream)
 {
     if (!c) return fail(nullptr, USPG_EINVAL, "NULL context");
+    if (c->store_src) return fail(c, USPG_EUNSUPPORTED, "this context reads another context's store");
     uspg_status st = ensure_state(c);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;

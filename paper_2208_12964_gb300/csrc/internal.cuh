@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 #include <map>
+#include <atomic>
 
 #include "../../include/uspg.h"
 
@@ -73,7 +74,7 @@ struct StoreView {
     const void *sw;               // cell-major weights
 };
 
-int64_t &launch_counter();
+std::atomic<int64_t> &launch_counter();  // kernels launched (host threads may launch concurrently)
 
 // ---- generator (generator.cu) ----
 struct GenOut {
@@ -161,6 +162,9 @@ struct uspg_ctx {
     std::map<std::string, uspg::Graph> graphs;
     int last_sweeps = 0;
     std::string err;
+    // set on a context that reads another context's store and tables (which
+    // must outlive it); its image, projections, scratch and graphs are its own
+    const uspg_ctx *store_src = nullptr;
 };
 
 namespace uspg {
@@ -171,6 +175,12 @@ uspg_status build_store(uspg_ctx *c, cudaStream_t s);
 uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s);
 uspg_status launch_backward_view(uspg_ctx *c, int view, float lambda, cudaStream_t s);
 uspg_status launch_sequential(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s);
+// device bytes currently held by a context (its own buffers only)
+long long ctx_device_bytes(const uspg_ctx *c);
+// a new context on src's grid, scan and built store, with its own image,
+// projections and scratch: one more reconstruction of src's geometry without
+// a second copy of the coefficients
+uspg_status ctx_share_store(const uspg_ctx *src, uspg_ctx **out);
 StoreView store_view(const uspg_ctx *c, int rep);
 // resample.cu
 uspg_status launch_resample(uspg_ctx *c, int mode, int nx, int ny, float *out, cudaStream_t s);

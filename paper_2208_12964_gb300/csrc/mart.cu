@@ -29,9 +29,9 @@
 
 namespace uspg {
 
-int64_t &launch_counter()
+std::atomic<int64_t> &launch_counter()
 {
-    static int64_t n = 0;
+    static std::atomic<int64_t> n{0};
     return n;
 }
 

@@ -23,6 +23,7 @@ F32, F16, BF16 = 0, 1, 2
 SEQUENTIAL, PER_VIEW = 0, 1
 POWER, LINEAR_EQ18 = 0, 1
 RESAMPLE_POINT, RESAMPLE_BIJECTION = 0, 1
+JOB_BORROW_PROJECTIONS = 1
 
 
 class UspgError(RuntimeError):
@@ -59,6 +60,23 @@ class Stats(C.Structure):
                                          "nnz_all_views", "store_bytes", "full_matrix_bytes", "max_row", "gcd")]
 
 
+class Job(C.Structure):
+    _fields_ = [("grid", GridDesc), ("scan", ScanDesc), ("coeff", CoeffOpts), ("mart", MartOpts),
+                ("projections", C.c_void_p), ("f0", C.c_float), ("flags", C.c_int32)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("reused_store", C.c_int32), ("n_cells", C.c_int64), ("updates", C.c_int64),
+                ("queue_s", C.c_double), ("run_s", C.c_double), ("latency_s", C.c_double),
+                ("message", C.c_char * 200)]
+
+
+class ServerReport(C.Structure):
+    _fields_ = ([(n, C.c_int64) for n in ("submitted", "completed", "failed", "queued", "active", "store_reuses",
+                                          "device_bytes", "peak_device_bytes")]
+                + [(n, C.c_double) for n in ("p50_s", "p99_s", "mean_s", "jobs_per_s", "updates_per_s")])
+
+
 _lib = None
 
 
@@ -93,6 +111,12 @@ def lib():
             "uspg_batch_run": ([V, V], I32),
             "uspg_batch_info": ([V, P(I64), P(I64), P(I64)], I32),
             "uspg_batch_destroy": ([V], None),
+            "uspg_server_create": ([C.c_size_t, I32, I32, P(V)], I32),
+            "uspg_server_submit": ([V, P(Job), P(C.c_uint64)], I32),
+            "uspg_server_poll": ([V, C.c_uint64, V, P(JobResult)], I32),
+            "uspg_server_drain": ([V, C.c_double], I32),
+            "uspg_server_stats": ([V, P(ServerReport)], I32),
+            "uspg_server_destroy": ([V], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -286,3 +310,60 @@ def uspg_batch_info(batch) -> dict:
 
 def uspg_batch_destroy(batch):
     lib().uspg_batch_destroy(batch)
+
+
+def uspg_server_create(device_budget: int, max_active: int, chunk_sweeps: int):
+    """Reconstruction server on the current device (scheduler and preparer
+    threads in the library)."""
+    h = C.c_void_p()
+    _check(lib().uspg_server_create(device_budget, max_active, chunk_sweeps, C.byref(h)), None)
+    return h.value
+
+
+def uspg_server_submit(server, spec: dict, projections, opts: MartOpts, dtype: int = F32,
+                       weight_mode: int = LENGTH, f0: float = 1.0, borrow: bool = False) -> int:
+    """Queues one reconstruction of workload ``spec`` (see synth.workload) with
+    host float32 ``projections`` [views][rays] (a numpy array, or a host torch
+    tensor); returns the job id.  borrow: the server reads ``projections`` in
+    place, so the caller keeps it unchanged until the job has been polled."""
+    g, s, o, keep = descs_from_spec(spec, dtype, weight_mode)
+    if isinstance(projections, np.ndarray):
+        projections = np.ascontiguousarray(projections, np.float32)
+        addr = projections.ctypes.data
+    else:
+        if not projections.is_contiguous() or projections.is_cuda or str(projections.dtype) != "torch.float32":
+            raise ValueError("projections: contiguous host float32")
+        addr = int(projections.data_ptr())
+    job = Job(grid=g, scan=s, coeff=o, mart=opts, projections=addr, f0=f0,
+              flags=JOB_BORROW_PROJECTIONS if borrow else 0)
+    jid = C.c_uint64(0)
+    _check(lib().uspg_server_submit(server, C.byref(job), C.byref(jid)), None)
+    del keep
+    return jid.value
+
+
+def uspg_server_poll(server, job_id: int, image: np.ndarray | None = None):
+    """None while the job runs; else its result as a dict (``status`` is the
+    job's own outcome) with the image written into ``image`` (host float32)."""
+    r = JobResult()
+    st = lib().uspg_server_poll(server, job_id, _ptr(image), C.byref(r))
+    if st == ENOTREADY:
+        return None
+    _check(st, None)
+    out = {n: getattr(r, n) for n, _ in JobResult._fields_}
+    out["message"] = r.message.decode(errors="replace")
+    return out
+
+
+def uspg_server_drain(server, timeout_s: float):
+    _check(lib().uspg_server_drain(server, timeout_s), None)
+
+
+def uspg_server_stats(server) -> dict:
+    r = ServerReport()
+    _check(lib().uspg_server_stats(server, C.byref(r)), None)
+    return {n: getattr(r, n) for n, _ in ServerReport._fields_}
+
+
+def uspg_server_destroy(server):
+    lib().uspg_server_destroy(server)

@@ -86,3 +86,13 @@ def test_oracle_and_library_share_no_source():
         assert "oracle" not in text.lower() or "oracle" not in re.findall(r'#include\s+"([^"]+)"', text), f
     orc = open(os.path.join(ROOT, "oracle", "uspg_oracle.c")).read()
     assert "#include \"" not in orc  # only system headers
+
+
+def test_server_create_validates_on_host(U):
+    for budget, active, chunk in ((0, 2, 4), (1 << 30, 0, 4), (1 << 30, 2, 0)):
+        with pytest.raises(U.UspgError) as e:
+            U.uspg_server_create(budget, active, chunk)
+        assert e.value.status == U.EINVAL
+    with pytest.raises(U.UspgError) as e:
+        U._check(U.lib().uspg_server_submit(None, None, None))
+    assert e.value.status == U.EINVAL

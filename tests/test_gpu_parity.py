@@ -17,14 +17,6 @@ TOL_W = 1e-6
 TOL_IMG = 1e-4
 
 
-@pytest.fixture(scope="module")
-def torch_cuda():
-    import torch
-
-    assert torch.cuda.is_available()
-    return torch
-
-
 # -------------------------------------------------------------- generator ---
 
 def test_rows_2d_parallel_all_views_all_rays(torch_cuda):
