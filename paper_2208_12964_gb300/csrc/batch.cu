@@ -66,7 +66,7 @@ __global__ void k_batch_finalize(const BatchInst *__restrict__ inst, long long s
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(256) k_batch_backward(const BatchInst *__restrict__ inst, long long step,
+__global__ void __launch_bounds__(256, kBwdMinBlocks) k_batch_backward(const BatchInst *__restrict__ inst, long long step,
                                                         float lambda)
 {
     const BatchInst &I = inst[blockIdx.y];

@@ -198,6 +198,11 @@ __device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, cons
     }
 }
 
+// The correction is latency-bound (about 1.6 entries per cell and view):
+// 8 resident blocks of 256 threads (32 registers a thread, 64 warps per SM)
+// hide more of it than fewer, fatter warps.
+constexpr int kBwdMinBlocks = 8;
+
 // Correction of slices wg, wg + W, ... of one representative (lane-ordered
 // cell-major store): each lane owns one cell; the next slice's descriptor
 // loads are issued before the current slice's gathers; the unrolled row loop
@@ -224,8 +229,9 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
         int sec = cell_sector(cur.m) + (int)(cur.d >> 11);
         int s2 = sec + mG * re.step;
         s2 = s2 >= re.ng ? s2 - re.ng : s2;
-        long long cell = (long long)cell_slab(cur.m) * cps + re.head + s2;
-        float fv = cnt > 0 ? f[cell] : 0.0f;
+        // cell ids are below 2^31 (checked at context creation): 32-bit index math
+        float *fp = f + (uint32_t)(cell_slab(cur.m) * (uint32_t)cps + (uint32_t)re.head + (uint32_t)s2);
+        float fv = cnt > 0 ? *fp : 0.0f;
         uint32_t off = cur.off + lane;
         load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
         float num = 0.f, den = 0.f;
@@ -247,7 +253,7 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
                 num += (act && !zr) ? wt * r : 0.0f;
             }
         }
-        if (den > 0.0f) f[cell] = zero ? 0.0f : fv * expf(lambda * (num / den));
+        if (den > 0.0f) *fp = zero ? 0.0f : fv * expf(lambda * (num / den));
         cur = nxt;
     }
 }

@@ -95,7 +95,7 @@ __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__rest
 // lane 0's (lanes are ordered by count), so the unrolled row loop is sized
 // per slice (warp-uniform) to 2, 4 or 8 rows, with a loop beyond.
 template <typename WT>
-__global__ void __launch_bounds__(256) k_backward_sell(const long long *__restrict__ slice_off, long long base,
+__global__ void __launch_bounds__(256, kBwdMinBlocks) k_backward_sell(const long long *__restrict__ slice_off, long long base,
                                                        const uint32_t *__restrict__ slice_meta,
                                                        const uint16_t *__restrict__ lane_desc,
                                                        const uint32_t *__restrict__ cray, const WT *__restrict__ cw,
