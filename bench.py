@@ -266,21 +266,23 @@ def run_ours(args, rank, world, local):
 
 
 def roofline(info):
-    """Dominant per-view kernel: algorithmic bytes per launch / mean launch time."""
+    """Dominant per-view kernel: algorithmic HBM bytes per launch / mean launch time.
+
+    Per view, with S = entries the representative stores (half of the view's
+    nonzeros under the z-mirror), b = index + weight bytes per entry:
+      forward:    S*b (rows) + S/8*4 (group rays) + rays*12 (projection in,
+                  ray sum accumulate, log-ratio out); the image gathers hit L2
+      correction: S*b (columns) + slices*76 (offset, meta, lane table)
+                  + cells*8 (image read and write) + rays*4 (log-ratios)
+    """
     st = info["stats"]
-    spec = info["spec"]
     fw, bw = np.asarray(info["fw"], np.float64), np.asarray(info["bw"], np.float64)
     n_rays = st["n_rays"]
-    reps = st["n_reps"]
-    nnz_view = st["nnz_all_views"] / st["n_views"]
-    wb = info.get("weight_bytes", 4)
-    # forward: stream the representative rows (index + weight), row pointers,
-    # projections in, per-ray log ratio out; the image (25 MB) is L2-resident
-    fwd_bytes = nnz_view * (4 + wb) + n_rays * (8 + 4 + 4)
-    # backward: stream the cell-major entries (ray id + weight), slice
-    # descriptors, and read+write every image cell once
+    S = st["nnz_store"] / st["n_reps"]
+    b_e = 4 + info.get("weight_bytes", 4)
     cells = st["n_cells"]
-    bwd_bytes = nnz_view * (4 + wb) + cells * (4 + 4)
+    fwd_bytes = S * b_e + S / 8 * 4 + n_rays * 12
+    bwd_bytes = S * b_e + st["slices"] * 76 + cells * 8 + n_rays * 4
     t_f, t_b = fw.mean(), bw.mean()
     if t_b >= t_f:
         name, b, t = "k_backward", bwd_bytes, t_b
@@ -293,7 +295,8 @@ def roofline(info):
             "bytes_per_launch": int(b), "ms_per_launch": round(t, 5),
             "other": {"k_forward_ms": round(t_f, 5), "k_backward_ms": round(t_b, 5),
                       "k_forward_GBs": round(fwd_bytes / (t_f * 1e-3) / 1e9, 1),
-                      "k_backward_GBs": round(bwd_bytes / (t_b * 1e-3) / 1e9, 1)}}
+                      "k_backward_GBs": round(bwd_bytes / (t_b * 1e-3) / 1e9, 1),
+                      "mirrored_store": bool(st["mirrored"])}}
 
 
 # ------------------------------------------------------------- oracle ---

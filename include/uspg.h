@@ -129,6 +129,8 @@ typedef struct {
     int64_t full_matrix_bytes; /* bytes the same layouts would need for every view */
     int64_t max_row;           /* longest row (entries) */
     int64_t gcd;               /* rotational symmetry order G of the grid */
+    int64_t mirrored;          /* 1: z-mirror store (only the lower detector rows and slabs are held) */
+    int64_t slices;            /* cell-major slices (32 cells) per representative */
 } uspg_stats;
 
 /* --- context -------------------------------------------------------------- */

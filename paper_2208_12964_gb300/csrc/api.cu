@@ -93,7 +93,8 @@ static uspg_status alloc_state(uspg_ctx *c)
     if (c->d_f) return USPG_OK;
     USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * c->n_cells));
     USPG_CUDA(c, cudaMalloc(&c->d_proj, sizeof(float) * (long long)c->scan.n_views * c->n_rays));
-    USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * c->n_rays));
+    // per-ray log-ratios; mirrored stores keep them as pairs per stored ray
+    USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * std::max<long long>(c->n_rays, 2LL * c->mir.n_rows)));
     USPG_CUDA(c, cudaMalloc(&c->d_sacc, sizeof(float) * c->n_rays));
     USPG_CUDA(c, cudaMemset(c->d_sacc, 0, sizeof(float) * c->n_rays));
     USPG_CUDA(c, cudaMalloc(&c->d_status, sizeof(int)));
@@ -134,7 +135,9 @@ static uspg_status ensure_state(uspg_ctx *c)
         chunk += (c->ng[i] + kSlice - 1) / kSlice;
     }
     c->slices_per_slab = chunk;
-    c->slices_per_rep = (long long)chunk * (c->scan.geometry == USPG_CONE_3D ? c->n_slabs : 1);
+    // cell-major store: all slabs, or the lower half and the middle slab when mirrored
+    int stored_slabs = c->scan.geometry == USPG_CONE_3D ? (c->mir.on ? (c->n_slabs + 1) / 2 : c->n_slabs) : 1;
+    c->slices_per_rep = (long long)chunk * stored_slabs;
     USPG_CUDA(c, cudaMalloc(&c->d_ring, sizeof(RingEntry) * c->n_rings));
     USPG_CUDA(c, cudaMemcpy(c->d_ring, rt.data(), sizeof(RingEntry) * c->n_rings, cudaMemcpyHostToDevice));
     return alloc_state(c);
@@ -169,8 +172,8 @@ uspg_status ctx_share_store(const uspg_ctx *src, uspg_ctx **out)
 long long ctx_device_bytes(const uspg_ctx *c)
 {
     int wb = c->dtype == USPG_F32 ? 4 : 2;
-    long long rows = (long long)c->n_reps * c->n_rays, slices = c->slices_per_rep * c->n_reps;
-    long long b = 4LL * c->n_cells + 4LL * c->scan.n_views * c->n_rays + 8LL * c->n_rays;  // image, projections, scratch
+    long long rows = (long long)c->n_reps * c->mir.n_rows, slices = c->slices_per_rep * c->n_reps;
+    long long b = 4LL * c->n_cells + 4LL * c->scan.n_views * c->n_rays + 12LL * c->n_rays;  // image, projections, scratch
     if (c->store_src) return b;
     b += (long long)sizeof(RingEntry) * c->n_rings + 24LL * c->cells_per_slab;  // ring table, boundaries
     if (c->d_row_ptr) {
@@ -240,6 +243,14 @@ uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, 
     c->z_min = s.geometry == USPG_CONE_3D ? g.z_min : 0.0;
     c->scan = s;
     c->n_rays = s.n_u * (s.geometry == USPG_CONE_3D ? s.n_v : 1);
+    // z-mirror (Sec. III.C symmetry): a cone scan whose source lies on the
+    // mid-plane of a slab stack centred on z = 0 stores only detector rows
+    // v < (n_v+1)/2; row n_v-1-v is the same row with slab s -> n_s-1-s
+    c->mir.n_u = s.n_u;
+    c->mir.n_v = s.geometry == USPG_CONE_3D ? s.n_v : 1;
+    c->mir.n_slabs = ns;
+    c->mir.on = s.geometry == USPG_CONE_3D && s.n_v >= 2 && c->z_min == -0.5 * (double)ns * c->h;
+    c->mir.n_rows = c->mir.on ? (s.n_v + 1) / 2 * s.n_u : c->n_rays;
     c->weight_mode = wm;
     c->dtype = dt;
     double unit = c->r;
@@ -381,14 +392,18 @@ uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
     o->n_reps = c->n_reps;
     o->nnz_store = c->gen.nnz;
     o->nnz_all_views = c->nnz_all_views;
-    long long rows = (long long)c->n_reps * c->n_rays;
+    long long rows = (long long)c->n_reps * c->mir.n_rows;
     long long slices = c->slices_per_rep * c->n_reps;
     o->store_bytes = c->gen.nnz_pad * (4 + wb) + (rows + 1) * 8 + rows * 4 + c->gen.sell_entries * (4 + wb) +
                      slices * (8 + 4 + 4);
+    // the same layouts for every view, and without the z-mirror
     double per_view = c->n_reps ? (double)o->store_bytes / c->n_reps : 0.0;
-    o->full_matrix_bytes = (int64_t)(per_view * c->scan.n_views);
+    double unmirrored = c->gen.nnz ? (double)c->gen.nnz_reps_full / (double)c->gen.nnz : 1.0;
+    o->full_matrix_bytes = (int64_t)(per_view * unmirrored * c->scan.n_views);
     o->max_row = c->gen.max_row;
     o->gcd = c->G;
+    o->mirrored = c->mir.on;
+    o->slices = c->slices_per_rep;
     return USPG_OK;
 }
 
@@ -400,9 +415,11 @@ uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t 
     if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
     if (view < 0 || view >= c->scan.n_views || ray < 0 || ray >= c->n_rays) return fail(c, USPG_EINVAL, "bad view/ray");
     int rep = c->rep_of_view[view];
-    long long row = (long long)rep * c->n_rays + ray;
+    bool flip = c->mir.on && ray >= c->mir.n_rows;  // a mirrored row: stored as its mirror ray
+    int stored = flip ? mirror_ray(ray, c->mir.n_u, c->mir.n_v) : ray;
+    long long row = (long long)rep * c->mir.n_rows + stored;
     if (c->h_row_ptr.empty()) {
-        long long nrows = (long long)c->n_reps * c->n_rays;
+        long long nrows = (long long)c->n_reps * c->mir.n_rows;
         c->h_row_ptr.resize(nrows + 1);
         USPG_CUDA(c, cudaMemcpy(c->h_row_ptr.data(), c->d_row_ptr, sizeof(long long) * (nrows + 1),
                                 cudaMemcpyDeviceToHost));
@@ -439,7 +456,7 @@ uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t 
         }
         if (!(wv > 0.0)) continue;  // row padding
         if (cnt < cap && cells && w) {
-            uint32_t pc = ix[q];
+            uint32_t pc = flip ? flip_slab(ix[q], c->n_slabs) : ix[q];
             int ring = cell_ring(pc), ng = c->ng[ring];
             int sec = (cell_sector(pc) + mG * (ng / c->G)) % ng;
             cells[cnt] = (long long)cell_slab(pc) * c->cells_per_slab + c->head[ring] + sec;

@@ -38,6 +38,7 @@ struct BatchInst {
     long long cps, S, steps;
     int n_rings, n_rays, n_views, fwd_blocks, bwd_blocks;
     float w_scale;
+    Mirror mir;  // z-mirror store of the instance (mir.on == 0: every row stored)
 };
 
 template <typename WT>
@@ -50,9 +51,14 @@ __global__ void __launch_bounds__(256) k_batch_forward(const BatchInst *__restri
     int rep = I.view_rep[view];
     fill_tab(tab, I.rt, I.n_rings, I.view_mg[view], threadIdx.x, blockDim.x);
     __syncthreads();
-    fwd_groups<WT>(I.idx, (const WT *)I.w, I.grp_ray, I.rep_g0[rep], I.rep_ng[rep], I.f, tab, I.cps, I.sacc,
-                   ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((long long)I.fwd_blocks * blockDim.x) >> 5,
-                   threadIdx.x & 31);
+    long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long W = ((long long)I.fwd_blocks * blockDim.x) >> 5;
+    if (I.mir.on)  // block-uniform
+        fwd_groups<WT, true>(I.idx, (const WT *)I.w, I.grp_ray, I.rep_g0[rep], I.rep_ng[rep], I.f, tab, I.cps, I.sacc,
+                             wg, W, threadIdx.x & 31, I.mir);
+    else
+        fwd_groups<WT, false>(I.idx, (const WT *)I.w, I.grp_ray, I.rep_g0[rep], I.rep_ng[rep], I.f, tab, I.cps,
+                              I.sacc, wg, W, threadIdx.x & 31, I.mir);
 }
 
 __global__ void k_batch_finalize(const BatchInst *__restrict__ inst, long long step)
@@ -60,23 +66,32 @@ __global__ void k_batch_finalize(const BatchInst *__restrict__ inst, long long s
     const BatchInst &I = inst[blockIdx.y];
     if (step >= I.steps) return;
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray >= I.n_rays) return;
+    if (ray >= I.mir.n_rows) return;  // the stored rays (all rays when not mirrored)
     int view = (int)(step % I.n_views);
-    finalize_ray(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.w_scale, nullptr, I.res);
+    if (I.mir.on)
+        finalize_pair(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.mir, I.w_scale, nullptr, (float2 *)I.res);
+    else
+        finalize_ray(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.w_scale, nullptr, I.res);
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(256, kBwdMinBlocks) k_batch_backward(const BatchInst *__restrict__ inst, long long step,
-                                                        float lambda)
+__global__ void __launch_bounds__(256, kBwdMinBlocksMirror) k_batch_backward(const BatchInst *__restrict__ inst,
+                                                                             long long step, float lambda)
 {
     const BatchInst &I = inst[blockIdx.y];
     if (step >= I.steps || (int)blockIdx.x >= I.bwd_blocks) return;
     int view = (int)(step % I.n_views);
     int rep = I.view_rep[view];
-    bwd_slices<WT>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
-                   I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt, I.view_mg[view], I.cps,
-                   I.S, lambda, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                   ((long long)I.bwd_blocks * blockDim.x) >> 5, threadIdx.x & 31);
+    long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long W = ((long long)I.bwd_blocks * blockDim.x) >> 5;
+    if (I.mir.on)  // block-uniform
+        bwd_slices<WT, true>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
+                             I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt,
+                             I.view_mg[view], I.cps, I.S, lambda, wg, W, threadIdx.x & 31, I.mir);
+    else
+        bwd_slices<WT, false>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
+                              I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt,
+                              I.view_mg[view], I.cps, I.S, lambda, wg, W, threadIdx.x & 31, I.mir);
 }
 
 }  // namespace uspg
@@ -241,6 +256,7 @@ uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_
         I.n_rays = c->n_rays;
         I.n_views = V;
         I.w_scale = (float)c->w_scale;
+        I.mir = c->mir;
         b->groups_view[i] = std::max<long long>(1, gsum / V);
         b->slices_view[i] = std::max<long long>(1, I.S);
         b->max_steps = std::max(b->max_steps, I.steps);

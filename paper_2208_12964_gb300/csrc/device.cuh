@@ -100,11 +100,15 @@ __device__ __forceinline__ void load_group(Group8<WT> &G, const uint32_t *idx, c
 // tab: ring table {head, ng, shift} of the view.  Each lane takes one group;
 // the next chunk's stream loads are issued before the current chunk's image
 // gathers, and lanes of the same ray are combined by a segmented shuffle sum.
-template <typename WT>
+// MIR (z-mirror store): every stored row also yields the sum of its mirror
+// ray, from the same entries with the slab flipped; a row that is its own
+// mirror adds once.
+template <typename WT, bool MIR>
 __device__ __forceinline__ void fwd_groups(const uint32_t *__restrict__ idx, const WT *__restrict__ w,
                                            const uint32_t *__restrict__ grp_ray, long long g0, long long n_groups,
                                            const float *__restrict__ f, const int4 *tab, long long cps,
-                                           float *__restrict__ sacc, long long wg, long long W, int lane)
+                                           float *__restrict__ sacc, long long wg, long long W, int lane,
+                                           const Mirror &M)
 {
     const long long step = W * 32;
     long long base = wg * 32;
@@ -114,43 +118,85 @@ __device__ __forceinline__ void fwd_groups(const uint32_t *__restrict__ idx, con
     for (; base < n_groups; base += step) {
         long long nb = base + step;
         load_group(nxt, idx, w, grp_ray, g0 + nb + lane, nb + lane < n_groups);
-        float gv[8];
+        float acc = 0.0f, accm = 0.0f;
+        if (MIR) {
+            float gv[8], gm[8];
 #pragma unroll
-        for (int i = 0; i < 8; i++) gv[i] = cur.w[i] != 0.0f ? __ldg(f + rot_cell(tab, cps, cur.c[i])) : 0.0f;
-        float acc = 0.0f;
+            for (int i = 0; i < 8; i++) {
+                bool on = cur.w[i] != 0.0f;
+                long long cl = rot_cell(tab, cps, cur.c[i]);
+                long long cm = cl + (long long)(M.n_slabs - 1 - 2 * cell_slab(cur.c[i])) * cps;
+                gv[i] = on ? __ldg(f + cl) : 0.0f;
+                gm[i] = on ? __ldg(f + cm) : 0.0f;
+            }
 #pragma unroll
-        for (int i = 0; i < 8; i++) acc = fmaf(cur.w[i], gv[i], acc);
+            for (int i = 0; i < 8; i++) {
+                acc = fmaf(cur.w[i], gv[i], acc);
+                accm = fmaf(cur.w[i], gm[i], accm);
+            }
+        } else {
+            float gv[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) gv[i] = cur.w[i] != 0.0f ? __ldg(f + rot_cell(tab, cps, cur.c[i])) : 0.0f;
+#pragma unroll
+            for (int i = 0; i < 8; i++) acc = fmaf(cur.w[i], gv[i], acc);
+        }
         uint32_t ray = cur.ray;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             float v2 = __shfl_down_sync(0xffffffffu, acc, o);
+            float m2 = MIR ? __shfl_down_sync(0xffffffffu, accm, o) : 0.0f;
             uint32_t r2 = __shfl_down_sync(0xffffffffu, ray, o);
-            if (lane + o < 32 && r2 == ray) acc += v2;
+            if (lane + o < 32 && r2 == ray) {
+                acc += v2;
+                accm += m2;
+            }
         }
         uint32_t rprev = __shfl_up_sync(0xffffffffu, ray, 1);
-        if (ray != 0xffffffffu && (lane == 0 || rprev != ray)) atomicAdd(&sacc[ray], acc);
+        if (ray != 0xffffffffu && (lane == 0 || rprev != ray)) {
+            atomicAdd(&sacc[ray], acc);
+            if (MIR) {
+                int rm = mirror_ray((int)ray, M.n_u, M.n_v);
+                if (rm != (int)ray) atomicAdd(&sacc[rm], accm);
+            }
+        }
         cur = nxt;
     }
 }
 
+__device__ __forceinline__ float log_ratio(float sv, float p)
+{
+    // NaN marks a ray to skip (empty row or zero sum), -inf a ray with P = 0
+    if (!(sv > 0.0f)) return __int_as_float(0x7fc00000);
+    return p > 0.0f ? logf(p / sv) : -INFINITY;
+}
+
 // ln(P/Pbar) of one ray from its accumulated sum; clears the accumulator.
-// NaN marks a ray to skip (empty row or zero sum), -inf a ray with P = 0.
 __device__ __forceinline__ void finalize_ray(float *__restrict__ sacc, const float *__restrict__ proj, int ray,
                                              float w_scale, float *__restrict__ out_s, float *__restrict__ out_res)
 {
     float sv = sacc[ray] * w_scale;
     sacc[ray] = 0.0f;
     if (out_s) out_s[ray] = sv;
-    if (out_res) {
-        float res;
-        if (!(sv > 0.0f)) {
-            res = __int_as_float(0x7fc00000);
-        } else {
-            float p = proj[ray];
-            res = p > 0.0f ? logf(p / sv) : -INFINITY;
-        }
-        out_res[ray] = res;
+    if (out_res) out_res[ray] = log_ratio(sv, proj[ray]);
+}
+
+// z-mirror store: stored ray r and its mirror; out_res2[r] = {ln ratio of r,
+// ln ratio of mirror(r)} (the pair the correction gathers in one load).
+__device__ __forceinline__ void finalize_pair(float *__restrict__ sacc, const float *__restrict__ proj, int ray,
+                                              const Mirror &M, float w_scale, float *__restrict__ out_s,
+                                              float2 *__restrict__ out_res2)
+{
+    int rm = mirror_ray(ray, M.n_u, M.n_v);
+    float sv = sacc[ray] * w_scale;
+    float sm = rm != ray ? sacc[rm] * w_scale : sv;
+    sacc[ray] = 0.0f;
+    sacc[rm] = 0.0f;
+    if (out_s) {
+        out_s[ray] = sv;
+        out_s[rm] = sm;
     }
+    if (out_res2) out_res2[ray] = make_float2(log_ratio(sv, proj[ray]), log_ratio(sm, proj[rm]));
 }
 
 struct SliceDesc {
@@ -172,13 +218,30 @@ __device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_o
     }
 }
 
-// rows 0..R-1 of one lane: loads first, then the ray-value gathers
-template <typename WT, int R>
+__device__ __forceinline__ void acc_entry(float wt, float r, float &num, float &den, bool &zero)
+{
+    bool act = (wt > 0.0f) && (r == r);  // NaN: the ray is skipped
+    bool zr = act && (r == -INFINITY);   // P = 0: the cell is zeroed
+    den += act ? wt : 0.0f;
+    zero |= zr;
+    num += (act && !zr) ? wt * r : 0.0f;
+}
+
+// Per-lane correction sums of one cell (and, MIR, of its mirror cell).
+struct CellSums {
+    float num, den, numm, denm;
+    bool zero, zerom;
+};
+
+// rows 0..R-1 of one lane: loads first, then the ray-value gathers.  MIR:
+// the key's bit 31 says whether the cell sees the stored ray (pair .x) or
+// its mirror (pair .y); the mirror cell sees the other one.
+template <typename WT, bool MIR, int R>
 __device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, const float *res, uint32_t off, int cnt,
-                                        float &num, float &den, bool &zero)
+                                        CellSums &S)
 {
     uint32_t ry[R];
-    float wv[R], rv[R];
+    float wv[R];
 #pragma unroll
     for (int t = 0; t < R; t++) {
         bool in = t < cnt;
@@ -186,15 +249,23 @@ __device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, cons
         ry[t] = in ? __ldcs(cray + pos) : 0u;
         wv[t] = in ? load_cs(cw, pos) : 0.0f;
     }
+    if (MIR) {
+        float2 rv[R];
 #pragma unroll
-    for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg(res + ry[t]) : 0.f;
+        for (int t = 0; t < R; t++)
+            rv[t] = t < cnt ? __ldg((const float2 *)res + (ry[t] & 0x7fffffffu)) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t = 0; t < R; t++) {
-        bool act = (wv[t] > 0.0f) && (rv[t] == rv[t]);
-        bool zr = act && (rv[t] == -INFINITY);
-        den += act ? wv[t] : 0.0f;
-        zero |= zr;
-        num += (act && !zr) ? wv[t] * rv[t] : 0.0f;
+        for (int t = 0; t < R; t++) {
+            bool up = ry[t] >> 31;
+            acc_entry(wv[t], up ? rv[t].y : rv[t].x, S.num, S.den, S.zero);
+            acc_entry(wv[t], up ? rv[t].x : rv[t].y, S.numm, S.denm, S.zerom);
+        }
+    } else {
+        float rv[R];
+#pragma unroll
+        for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg(res + ry[t]) : 0.f;
+#pragma unroll
+        for (int t = 0; t < R; t++) acc_entry(wv[t], rv[t], S.num, S.den, S.zero);
     }
 }
 
@@ -202,19 +273,22 @@ __device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, cons
 // 8 resident blocks of 256 threads (32 registers a thread, 64 warps per SM)
 // hide more of it than fewer, fatter warps.
 constexpr int kBwdMinBlocks = 8;
+constexpr int kBwdMinBlocksMirror = 6;  // the mirrored form holds two cells per lane
 
 // Correction of slices wg, wg + W, ... of one representative (lane-ordered
 // cell-major store): each lane owns one cell; the next slice's descriptor
 // loads are issued before the current slice's gathers; the unrolled row loop
-// is sized per slice from lane 0's (widest) count.
-template <typename WT>
+// is sized per slice from lane 0's (widest) count.  MIR: the store holds the
+// lower-half and middle slabs; a lane also updates the mirror cell (slab
+// n_s-1-s) from the same column, except in the middle slab.
+template <typename WT, bool MIR>
 __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_off, long long base,
                                            const uint32_t *__restrict__ slice_meta,
                                            const uint16_t *__restrict__ lane_desc, const uint32_t *__restrict__ cray,
                                            const WT *__restrict__ cw, const float *__restrict__ res,
                                            float *__restrict__ f, const RingEntry *__restrict__ rt, int mG,
                                            long long cps, long long n_slices, float lambda, long long wg, long long W,
-                                           int lane)
+                                           int lane, const Mirror &M)
 {
     long long sl = wg;
     if (sl >= n_slices) return;
@@ -230,30 +304,39 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
         int s2 = sec + mG * re.step;
         s2 = s2 >= re.ng ? s2 - re.ng : s2;
         // cell ids are below 2^31 (checked at context creation): 32-bit index math
-        float *fp = f + (uint32_t)(cell_slab(cur.m) * (uint32_t)cps + (uint32_t)re.head + (uint32_t)s2);
+        int slab = cell_slab(cur.m);
+        uint32_t within = (uint32_t)re.head + (uint32_t)s2;
+        float *fp = f + (uint32_t)(slab * (uint32_t)cps + within);
+        bool pair = MIR && 2 * slab != M.n_slabs - 1;  // the middle slab is its own mirror
+        float *fq = MIR ? f + (uint32_t)((M.n_slabs - 1 - slab) * (uint32_t)cps + within) : fp;
         float fv = cnt > 0 ? *fp : 0.0f;
+        float fm = (MIR && pair && cnt > 0) ? *fq : 0.0f;
         uint32_t off = cur.off + lane;
         load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
-        float num = 0.f, den = 0.f;
-        bool zero = false;
+        CellSums S{0.f, 0.f, 0.f, 0.f, false, false};
+        constexpr int RMAX = MIR ? 4 : 8;  // the mirrored form carries two cells: a shorter unroll
         if (width <= 2) {
-            cm_rows<WT, 2>(cr, cwb, res, off, cnt, num, den, zero);
+            cm_rows<WT, MIR, 2>(cr, cwb, res, off, cnt, S);
         } else if (width <= 4) {
-            cm_rows<WT, 4>(cr, cwb, res, off, cnt, num, den, zero);
+            cm_rows<WT, MIR, 4>(cr, cwb, res, off, cnt, S);
         } else {
-            cm_rows<WT, 8>(cr, cwb, res, off, cnt, num, den, zero);
-            for (int t = 8; t < cnt; t++) {  // long columns (cells close to the source)
+            cm_rows<WT, MIR, RMAX>(cr, cwb, res, off, cnt, S);
+            for (int t = RMAX; t < cnt; t++) {  // long columns (cells close to the source)
                 uint32_t pos = off + (uint32_t)t * kSlice;
                 float wt = load_cs(cwb, pos);
-                float r = __ldg(res + __ldcs(cr + pos));
-                bool act = (wt > 0.0f) && (r == r);
-                bool zr = act && (r == -INFINITY);
-                den += act ? wt : 0.0f;
-                zero |= zr;
-                num += (act && !zr) ? wt * r : 0.0f;
+                uint32_t key = __ldcs(cr + pos);
+                if (MIR) {
+                    float2 v = __ldg((const float2 *)res + (key & 0x7fffffffu));
+                    bool up = key >> 31;
+                    acc_entry(wt, up ? v.y : v.x, S.num, S.den, S.zero);
+                    acc_entry(wt, up ? v.x : v.y, S.numm, S.denm, S.zerom);
+                } else {
+                    acc_entry(wt, __ldg(res + key), S.num, S.den, S.zero);
+                }
             }
         }
-        if (den > 0.0f) *fp = zero ? 0.0f : fv * expf(lambda * (num / den));
+        if (S.den > 0.0f) *fp = S.zero ? 0.0f : fv * expf(lambda * (S.num / S.den));
+        if (MIR && pair && S.denm > 0.0f) *fq = S.zerom ? 0.0f : fm * expf(lambda * (S.numm / S.denm));
         cur = nxt;
     }
 }

@@ -42,47 +42,12 @@ __global__ void k_boundaries(const RingEntry *rt, int n_rings, double2 *bdir, fl
 
 // Upper bound on each row's length from the FP32 sizing walk.
 __global__ void __launch_bounds__(128) k_size(Geometry g, const RingEntry *rt, const float2 *bdirf,
-                                              const int *rep_view, int n_reps, int *caps, int mirror_from)
+                                              const int *rep_view, int n_reps, int *caps)
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)n_reps * g.n_rays) return;
-    int rep = (int)(gid / g.n_rays), ray = (int)(gid % g.n_rays);
-    if (mirror_from > 0 && ray / g.n_u >= mirror_from) ray = (g.n_v - 1 - ray / g.n_u) * g.n_u + ray % g.n_u;
+    if (gid >= (long long)n_reps * g.n_rows) return;
+    int rep = (int)(gid / g.n_rows), ray = (int)(gid % g.n_rows);
     caps[gid] = size_ray(g, rt, bdirf, rep_view[rep], ray);
-}
-
-// z-mirror of a cone scan about the mid-plane z = 0 (source on the plane,
-// slab stack centred on it): detector row c and row n_v-1-c see mirror-image
-// rays, whose crossings are the same and whose pieces lie in slab n_s-1-s.
-// Rows of the upper half are copied from their mirror with the slab flipped.
-__global__ void k_mirror_rows(int n_reps, int n_u, int n_v, int n_rays, int mirror_from, int n_slabs,
-                              const long long *row_ptr, int *counts, uint32_t *idx, double *w64, int *status)
-{
-    long long half = (long long)(n_v - mirror_from) * n_u;
-    long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per row
-    int lane = threadIdx.x & 31;
-    if (gid >= (long long)n_reps * half) return;
-    int rep = (int)(gid / half);
-    int q = (int)(gid % half);
-    int c = mirror_from + q / n_u, a = q % n_u;
-    long long dst = (long long)rep * n_rays + (long long)c * n_u + a;
-    long long src = (long long)rep * n_rays + (long long)(n_v - 1 - c) * n_u + a;
-    long long sb = row_ptr[src], db = row_ptr[dst], de = row_ptr[dst + 1];
-    int n = counts[src];
-    if (db + n > de) {  // the bound is the source's, so this cannot happen
-        if (lane == 0) flag(status, kStatusBounds);
-        n = (int)(de - db);
-    }
-    for (int k = lane; k < n; k += 32) {
-        uint32_t pc = idx[sb + k];
-        idx[db + k] = pack_cell(n_slabs - 1 - cell_slab(pc), cell_ring(pc), cell_sector(pc));
-        w64[db + k] = w64[sb + k];
-    }
-    for (long long k = db + n + lane; k < de; k += 32) {
-        idx[k] = 0;
-        w64[k] = 0.0;
-    }
-    if (lane == 0) counts[dst] = n;
 }
 
 // Exact row lengths (the FP64 walk without storing); used only when a row
@@ -90,12 +55,11 @@ __global__ void k_mirror_rows(int n_reps, int n_u, int n_v, int n_rays, int mirr
 template <int MAXR>
 __global__ void __launch_bounds__(128) k_count(Geometry g, const RingEntry *rt, const double2 *bdir,
                                                const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                                               int *status, int mirror_from)
+                                               int *status)
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)n_reps * g.n_rays) return;
-    int rep = (int)(gid / g.n_rays), ray = (int)(gid % g.n_rays);
-    if (mirror_from > 0 && ray / g.n_u >= mirror_from) ray = (g.n_v - 1 - ray / g.n_u) * g.n_u + ray % g.n_u;
+    if (gid >= (long long)n_reps * g.n_rows) return;
+    int rep = (int)(gid / g.n_rows), ray = (int)(gid % g.n_rows);
     uint32_t in_cell[MAXR];
     double root[MAXR];
     CountSink sink;
@@ -111,13 +75,11 @@ __global__ void __launch_bounds__(128) k_count(Geometry g, const RingEntry *rt, 
 template <int MAXR>
 __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, const double2 *bdir,
                                               const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                                              const long long *row_ptr, uint32_t *idx, double *w64, int *status,
-                                              int mirror_from)
+                                              const long long *row_ptr, uint32_t *idx, double *w64, int *status)
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)n_reps * g.n_rays) return;
-    int rep = (int)(gid / g.n_rays), ray = (int)(gid % g.n_rays);
-    if (mirror_from > 0 && ray / g.n_u >= mirror_from) return;  // built by k_mirror_rows
+    if (gid >= (long long)n_reps * g.n_rows) return;
+    int rep = (int)(gid / g.n_rows), ray = (int)(gid % g.n_rows);
     long long b = row_ptr[gid], e = row_ptr[gid + 1];
     uint32_t in_cell[MAXR];
     int in_pos[MAXR];
@@ -141,21 +103,20 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
 template <int MAXR>
 static void launch_walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
                         const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                        const long long *row_ptr, uint32_t *idx, double *w64, int *status, int mirror_from)
+                        const long long *row_ptr, uint32_t *idx, double *w64, int *status)
 {
     if (fill)
-        k_fill<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status,
-                                          mirror_from);
+        k_fill<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status);
     else
-        k_count<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, status, mirror_from);
+        k_count<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, status);
 }
 
 static void walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
                  const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                 const long long *row_ptr, uint32_t *idx, double *w64, int *status, int mirror_from = 0)
+                 const long long *row_ptr, uint32_t *idx, double *w64, int *status)
 {
 #define USPG_WALK(M) \
-    launch_walk<M>(fill, grid, s, g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status, mirror_from)
+    launch_walk<M>(fill, grid, s, g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status)
     if (g.n_rings <= 64) USPG_WALK(64);
     else if (g.n_rings <= 128) USPG_WALK(128);
     else if (g.n_rings <= 256) USPG_WALK(256);
@@ -283,16 +244,49 @@ __device__ __forceinline__ long long rep_cell_id(const RingEntry *rt, long long 
     return (long long)cell_slab(pc) * cps + rt[cell_ring(pc)].head + cell_sector(pc);
 }
 
+// Columns of the cell-major store fed by the stored entry (ray r, cell pc):
+// up to two (column cell, key) pairs.  The key is the ray id; with the
+// z-mirror only lower-half and middle slabs have columns, and bit 31 of the
+// key marks an entry whose column cell sees the mirror ray (mirror_ray(r))
+// while the column cell's own mirror sees r.  An entry in an upper slab
+// feeds the column of its mirror cell; an entry in the middle slab (odd slab
+// count) feeds its own column twice, as r and as its mirror; a row that is
+// its own mirror (middle detector row) holds both halves itself, so its
+// upper entries feed nothing and its middle ones feed once.
+__device__ __forceinline__ int entry_columns(const Mirror &M, int r, uint32_t pc, uint32_t col[2], uint32_t key[2])
+{
+    col[0] = pc;
+    key[0] = (uint32_t)r;
+    if (!M.on) return 1;
+    int side = 2 * cell_slab(pc) - (M.n_slabs - 1);  // < 0 lower, 0 middle, > 0 upper
+    bool self = (M.n_v & 1) && ray_row(r, M.n_u) == (M.n_v - 1) / 2;
+    if (side < 0) return 1;
+    if (side > 0) {
+        if (self) return 0;
+        col[0] = flip_slab(pc, M.n_slabs);
+        key[0] = (uint32_t)r | 0x80000000u;
+        return 1;
+    }
+    if (self) return 1;
+    col[1] = pc;
+    key[1] = (uint32_t)r | 0x80000000u;
+    return 2;
+}
+
 // one warp per row (coalesced entries)
-__global__ void k_cell_count(const long long *row_ptr, const int *counts, const uint32_t *idx, int n_rays,
+__global__ void k_cell_count(const long long *row_ptr, const int *counts, const uint32_t *idx, int n_rows, Mirror M,
                              const RingEntry *rt, long long cps, int *cell_cnt)
 {
     long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
-    if (ray >= n_rays) return;
+    if (ray >= n_rows) return;
     long long b = row_ptr[ray];
     int n = counts[ray];
-    for (int q = lane; q < n; q += 32) atomicAdd(&cell_cnt[rep_cell_id(rt, cps, idx[b + q])], 1);
+    for (int q = lane; q < n; q += 32) {
+        uint32_t col[2], key[2];
+        int k = entry_columns(M, (int)ray, idx[b + q], col, key);
+        for (int t = 0; t < k; t++) atomicAdd(&cell_cnt[rep_cell_id(rt, cps, col[t])], 1);
+    }
 }
 
 // one warp per slice: width = max count over its 32 cells
@@ -326,22 +320,25 @@ __global__ void k_slice_width(const RingEntry *rt, int n_rings, int slices_per_s
 
 template <typename WT>
 __global__ void k_cell_scatter(const long long *row_ptr, const int *counts, const uint32_t *idx, const WT *w,
-                               int n_rays, const RingEntry *rt, long long cps, int slices_per_slab,
+                               int n_rows, Mirror M, const RingEntry *rt, long long cps, int slices_per_slab,
                                const long long *slice_off, int *cell_fill, uint32_t *sray, WT *sw)
 {
     long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int wl = threadIdx.x & 31;
-    if (ray >= n_rays) return;
+    if (ray >= n_rows) return;
     long long b = row_ptr[ray];
     int n = counts[ray];
     for (int q = wl; q < n; q += 32) {  // one warp per row
-        uint32_t pc = idx[b + q];
-        int lane;
-        long long sl = rep_cell_slice(rt, slices_per_slab, pc, &lane);
-        int slot = atomicAdd(&cell_fill[rep_cell_id(rt, cps, pc)], 1);
-        long long pos = slice_off[sl] + (long long)slot * kSlice + lane;
-        sray[pos] = (uint32_t)ray;
-        sw[pos] = w[b + q];
+        uint32_t col[2], key[2];
+        int k = entry_columns(M, (int)ray, idx[b + q], col, key);
+        for (int t = 0; t < k; t++) {
+            int lane;
+            long long sl = rep_cell_slice(rt, slices_per_slab, col[t], &lane);
+            int slot = atomicAdd(&cell_fill[rep_cell_id(rt, cps, col[t])], 1);
+            long long pos = slice_off[sl] + (long long)slot * kSlice + lane;
+            sray[pos] = key[t];
+            sw[pos] = w[b + q];
+        }
     }
 }
 
@@ -417,26 +414,37 @@ __global__ void k_cell_finish(long long n_slices, const long long *slice_off, co
     }
 }
 
-// stats[rep] += row lengths of that representative; stats[n_reps] = longest row
-__global__ void k_row_stats(const int *counts, long long n_rows, int n_rays, int n_reps, long long *stats)
+// stats[rep] += entries of that representative's full rows (a stored row
+// counts twice when its mirror row is not stored), stats[n_reps + rep] +=
+// stored entries, stats[2 n_reps] = longest row
+__global__ void k_row_stats(const int *counts, long long n_all, int n_rows, Mirror M, int n_reps, long long *stats)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int c = i < n_rows ? counts[i] : 0;
-    long long rep = i < n_rows ? i / n_rays : -1;
+    int c = i < n_all ? counts[i] : 0;
+    long long rep = i < n_all ? i / n_rows : -1;
+    int ray = i < n_all ? (int)(i % n_rows) : 0;
+    int mult = M.on && !((M.n_v & 1) && ray_row(ray, M.n_u) == (M.n_v - 1) / 2) ? 2 : 1;
     int mx = c;
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    unsigned long long *st = (unsigned long long *)stats;
     // warps whose rows all belong to one representative reduce first
     long long rep0 = __shfl_sync(0xffffffffu, rep, 0);
     bool uniform = __all_sync(0xffffffffu, rep == rep0) && rep0 >= 0;
-    unsigned long long *st = (unsigned long long *)stats;
     if (uniform) {
-        int sum = c;
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&st[rep0], (unsigned long long)sum);
+        int full = c * mult, sum = c;
+        for (int o = 16; o > 0; o >>= 1) {
+            full += __shfl_xor_sync(0xffffffffu, full, o);
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&st[rep0], (unsigned long long)full);
+            atomicAdd(&st[n_reps + rep0], (unsigned long long)sum);
+        }
     } else if (rep >= 0) {
-        atomicAdd(&st[rep], (unsigned long long)c);
+        atomicAdd(&st[rep], (unsigned long long)c * mult);
+        atomicAdd(&st[n_reps + rep], (unsigned long long)c);
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(&st[n_reps], (unsigned long long)mx);
+    if ((threadIdx.x & 31) == 0) atomicMax(&st[2 * n_reps], (unsigned long long)mx);
 }
 
 __global__ void k_set_off(long long *dst, const long long *rel, long long n, long long base)
@@ -483,11 +491,11 @@ __global__ void k_sort_lanes(long long n_slices, const uint32_t *meta, const int
 
 // ray of every aligned group of kRowPad entries of the ray-major store (rows
 // start and end on group boundaries, so a group never straddles two rays)
-__global__ void k_group_rays(const long long *row_ptr, long long n_rows, int n_rays, uint32_t *grp_ray)
+__global__ void k_group_rays(const long long *row_ptr, long long n_all, int n_rows, uint32_t *grp_ray)
 {
     long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= n_rows) return;
-    uint32_t ray = (uint32_t)(row % n_rays);
+    if (row >= n_all) return;
+    uint32_t ray = (uint32_t)(row % n_rows);
     for (long long g = row_ptr[row] / kRowPad; g < row_ptr[row + 1] / kRowPad; g++) grp_ray[g] = ray;
 }
 
@@ -515,9 +523,12 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     g.d_so = c->scan.src_to_axis;
     g.d_sd = c->scan.src_to_det;
     g.cells_per_slab = c->cells_per_slab;
+    g.n_rows = c->mir.n_rows;
+    const Mirror M = c->mir;
+    const int n_rows = M.n_rows;
 
     const int nreps = c->n_reps;
-    const long long nrows = (long long)nreps * c->n_rays;
+    const long long nrows = (long long)nreps * n_rows;
     const long long n_slices = c->slices_per_rep;
     if (!c->d_row_ptr) {  // geometry-sized buffers, allocated once
         USPG_CUDA(c, cudaMalloc(&c->d_rep_view, sizeof(int) * nreps));
@@ -531,27 +542,22 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_slice_off, sizeof(long long) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_meta, sizeof(uint32_t) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_width, sizeof(int) * n_slices * nreps));
-        USPG_CUDA(c, cudaMalloc(&c->d_stats, sizeof(long long) * (nreps + 1)));
+        USPG_CUDA(c, cudaMalloc(&c->d_stats, sizeof(long long) * (2 * nreps + 1)));
         c->store_moved = true;
     }
     int *d_rep_view = c->d_rep_view, *d_counts = c->d_counts;
 
     const int TB = 128;
-    // z-mirror: a cone scan whose source sits on the mid-plane of a centred
-    // slab stack traces only detector rows c < mirror_from
-    int mirror_from = 0;
-    if (g.geometry == USPG_CONE_3D && g.z_min == -0.5 * (double)g.n_slabs * g.h && g.n_v >= 2)
-        mirror_from = (g.n_v + 1) / 2;
+    // with the z-mirror only the rows of rays 0 .. n_rows-1 (lower detector rows) are traced and stored
     // rows sized by the FP32 bound, filled by the FP64 walk; if any row
     // outgrows its bound the exact FP64 count sizes the rows instead
     long long nnz_pad = 0;
     for (int attempt = 0; attempt < 2; attempt++) {
         if (attempt == 0) {
-            k_size<<<nblk(nrows, TB), TB, 0, s>>>(g, c->d_ring, c->d_bdirf, d_rep_view, nreps, d_counts,
-                                                  mirror_from);
+            k_size<<<nblk(nrows, TB), TB, 0, s>>>(g, c->d_ring, c->d_bdirf, d_rep_view, nreps, d_counts);
         } else {
             walk(false, nblk(nrows, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, nreps, d_counts,
-                 nullptr, nullptr, nullptr, c->d_status, mirror_from);
+                 nullptr, nullptr, nullptr, c->d_status);
         }
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
@@ -573,16 +579,9 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
             c->store_moved = true;
         }
         walk(true, nblk(nrows, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, nreps, d_counts,
-             c->d_row_ptr, c->d_idx, c->d_w64, c->d_status, mirror_from);
+             c->d_row_ptr, c->d_idx, c->d_w64, c->d_status);
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
-        if (mirror_from > 0) {
-            long long nm = (long long)nreps * (g.n_v - mirror_from) * g.n_u;
-            k_mirror_rows<<<nblk(nm * 32, 256), 256, 0, s>>>(nreps, g.n_u, g.n_v, g.n_rays, mirror_from, g.n_slabs,
-                                                        c->d_row_ptr, d_counts, c->d_idx, c->d_w64, c->d_status);
-            launch_counter()++;
-            USPG_CUDA(c, cudaGetLastError());
-        }
         int st = 0;
         USPG_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         USPG_CUDA(c, cudaStreamSynchronize(s));
@@ -599,22 +598,25 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     USPG_CUDA(c, cudaGetLastError());
 
     // statistics on the device: per-representative nonzeros and longest row
-    USPG_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(long long) * (nreps + 1), s));
-    k_row_stats<<<nblk(nrows, 256), 256, 0, s>>>(d_counts, nrows, c->n_rays, nreps, c->d_stats);
+    USPG_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(long long) * (2 * nreps + 1), s));
+    k_row_stats<<<nblk(nrows, 256), 256, 0, s>>>(d_counts, nrows, n_rows, M, nreps, c->d_stats);
     launch_counter()++;
-    std::vector<long long> rep_nnz(nreps + 1);
-    USPG_CUDA(c, cudaMemcpyAsync(rep_nnz.data(), c->d_stats, sizeof(long long) * (nreps + 1), cudaMemcpyDeviceToHost,
-                                 s));
+    std::vector<long long> rep_nnz(2 * nreps + 1);
+    USPG_CUDA(c, cudaMemcpyAsync(rep_nnz.data(), c->d_stats, sizeof(long long) * (2 * nreps + 1),
+                                 cudaMemcpyDeviceToHost, s));
     USPG_CUDA(c, cudaStreamSynchronize(s));
-    long long nnz = 0, maxrow = rep_nnz[nreps];
-    for (int q = 0; q < nreps; q++) nnz += rep_nnz[q];
+    long long nnz = 0, nnz_full = 0, maxrow = rep_nnz[2 * nreps];
+    for (int q = 0; q < nreps; q++) {
+        nnz_full += rep_nnz[q];
+        nnz += rep_nnz[nreps + q];
+    }
     long long all = 0;
     for (int k = 0; k < c->scan.n_views; k++) all += rep_nnz[c->rep_of_view[k]];
     c->nnz_all_views = all;
     c->h_row_ptr.clear();  // host copy made on demand by uspg_get_row
     c->h_rep_entry0.assign(nreps + 1, 0);
     for (int q = 0; q <= nreps; q++)
-        USPG_CUDA(c, cudaMemcpyAsync(&c->h_rep_entry0[q], c->d_row_ptr + (long long)q * c->n_rays, sizeof(long long),
+        USPG_CUDA(c, cudaMemcpyAsync(&c->h_rep_entry0[q], c->d_row_ptr + (long long)q * n_rows, sizeof(long long),
                                      cudaMemcpyDeviceToHost, s));
 
     // cell-major store, one representative at a time
@@ -625,11 +627,11 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     c->h_sell_base.assign(nreps + 1, 0);
     for (int rep = 0; rep < nreps; rep++) {
         c->h_sell_base[rep] = sell;
-        const long long *rp = c->d_row_ptr + (long long)rep * c->n_rays;
-        const int *cn = d_counts + (long long)rep * c->n_rays;
+        const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
+        const int *cn = d_counts + (long long)rep * n_rows;
         USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
-        k_cell_count<<<nblk((long long)c->n_rays * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, c->n_rays, c->d_ring, c->cells_per_slab,
-                                                          d_cell_cnt);
+        k_cell_count<<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, n_rows, M, c->d_ring,
+                                                                       c->cells_per_slab, d_cell_cnt);
         launch_counter()++;
         int *wd = c->d_slice_width + rep * n_slices;
         uint32_t *md = c->d_slice_meta + rep * n_slices;
@@ -684,17 +686,17 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     }
     // pass 2: scatter each row entry to its cell's column, then sort and pad
     for (int rep = 0; rep < nreps; rep++) {
-        const long long *rp = c->d_row_ptr + (long long)rep * c->n_rays;
-        const int *cn = d_counts + (long long)rep * c->n_rays;
+        const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
+        const int *cn = d_counts + (long long)rep * n_rows;
         const long long *so = c->d_slice_off + rep * n_slices;
         USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
         USPG_CUDA(c, cudaMemsetAsync(d_cell_fill, 0, sizeof(int) * c->n_cells, s));
-        k_cell_count<<<nblk((long long)c->n_rays * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, c->n_rays, c->d_ring, c->cells_per_slab,
-                                                          d_cell_cnt);
+        k_cell_count<<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, n_rows, M, c->d_ring,
+                                                                       c->cells_per_slab, d_cell_cnt);
         launch_counter()++;
-        k_cell_scatter<WT><<<nblk((long long)c->n_rays * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, (const WT *)c->d_w, c->n_rays,
-                                                                c->d_ring, c->cells_per_slab, c->slices_per_slab, so,
-                                                                d_cell_fill, c->d_sray, (WT *)c->d_sw);
+        k_cell_scatter<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(
+            rp, cn, c->d_idx, (const WT *)c->d_w, n_rows, M, c->d_ring, c->cells_per_slab, c->slices_per_slab, so,
+            d_cell_fill, c->d_sray, (WT *)c->d_sw);
         launch_counter()++;
         k_cell_finish<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(n_slices, so, c->d_slice_width + rep * n_slices,
                                                                    c->d_slice_meta + rep * n_slices, c->d_ring,
@@ -715,13 +717,14 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         c->cap_grp = nnz_pad / kRowPad + 1;
         c->store_moved = true;
     }
-    k_group_rays<<<nblk(nrows, 256), 256, 0, s>>>(c->d_row_ptr, nrows, c->n_rays, c->d_grp_ray);
+    k_group_rays<<<nblk(nrows, 256), 256, 0, s>>>(c->d_row_ptr, nrows, n_rows, c->d_grp_ray);
     launch_counter()++;
 
     USPG_CUDA(c, cudaStreamSynchronize(s));
 
     c->gen.n_reps = nreps;
     c->gen.nnz = nnz;
+    c->gen.nnz_reps_full = nnz_full;
     c->gen.nnz_pad = nnz_pad;
     c->gen.sell_entries = sell;
     c->gen.max_row = maxrow;

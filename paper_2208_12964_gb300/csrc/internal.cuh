@@ -44,6 +44,28 @@ __host__ __device__ inline int cell_slab(uint32_t x) { return int(x >> 22); }
 __host__ __device__ inline int cell_ring(uint32_t x) { return int((x >> 12) & 1023u); }
 __host__ __device__ inline int cell_sector(uint32_t x) { return int(x & 4095u); }
 
+// z-mirror of a centred cone scan (source on the mid-plane z = 0 of a slab
+// stack centred on it): detector rows v and n_v-1-v see mirror-image rays,
+// whose pieces have the same lengths in slabs s and n_s-1-s.  Only the rows
+// v < (n_v+1)/2 are stored (ray ids below n_rows); the rest are their mirrors.
+struct Mirror {
+    int on;                // 0: every row is stored
+    int n_u, n_v, n_slabs;
+    int n_rows;            // stored rays per view (= n_rays when off)
+};
+
+__host__ __device__ inline uint32_t flip_slab(uint32_t pc, int n_slabs)
+{
+    return (uint32_t(n_slabs - 1 - cell_slab(pc)) << 22) | (pc & 0x3fffffu);
+}
+// detector row of a ray (ray = row * n_u + column)
+__host__ __device__ inline int ray_row(int ray, int n_u) { return ray / n_u; }
+// mirror image of a ray: row v -> n_v-1-v, same column
+__host__ __device__ inline int mirror_ray(int ray, int n_u, int n_v)
+{
+    return ray + (n_v - 1 - 2 * ray_row(ray, n_u)) * n_u;
+}
+
 // Per ring: first cell id in a slab (H_n of Eq. 2), sector count, and the
 // sector shift produced by one 1/G-turn rotation (n_g / G).
 struct RingEntry {
@@ -56,6 +78,7 @@ struct RingEntry {
 // Scan and grid geometry as the generator needs it (all by value).
 struct Geometry {
     int geometry, n_rings, n_slabs, n_u, n_v, n_rays, n_views, weight_mode;
+    int n_rows;  // traced rows per representative: rays 0 .. n_rows-1 (the lower detector rows when mirrored)
     long long arc_num, arc_den;
     double r, h, z_min, du, dv, d_so, d_sd;
     long long cells_per_slab;
@@ -80,6 +103,7 @@ std::atomic<int64_t> &launch_counter();  // kernels launched (host threads may l
 struct GenOut {
     int n_reps;
     long long nnz;      // unpadded entries
+    long long nnz_reps_full;  // entries of the representatives' full rows (mirrored rows counted)
     long long nnz_pad;  // padded ray-major entries
     long long sell_entries;
     long long max_row;
@@ -103,6 +127,7 @@ struct uspg_ctx {
     // scan
     uspg_scan_desc scan{};
     int n_rays = 0;
+    uspg::Mirror mir{};  // z-mirror: stored rows per view mir.n_rows (all rays when mir.on == 0)
     // coefficient options
     int weight_mode = USPG_LENGTH, dtype = USPG_F32;
     double w_scale = 1.0;  // stored weight = length / w_scale

@@ -35,21 +35,6 @@ std::atomic<int64_t> &launch_counter()
     return n;
 }
 
-StoreView store_view(const uspg_ctx *c, int rep)
-{
-    StoreView v;
-    v.row_ptr = c->d_row_ptr + (long long)rep * c->n_rays;
-    v.idx = c->d_idx;
-    v.w = c->d_w;
-    v.rowmax = c->d_rowmax + (long long)rep * c->n_rays;
-    v.slice_off = c->d_slice_off + (long long)rep * c->slices_per_rep;
-    v.slice_meta = c->d_slice_meta + (long long)rep * c->slices_per_rep;
-    v.slice_width = c->d_slice_width + (long long)rep * c->slices_per_rep;
-    v.sray = c->d_sray;
-    v.sw = c->d_sw;
-    return v;
-}
-
 // ---- per-view forward: entry-parallel ------------------------------------------
 //
 // Rows of the ray-major store start and end on multiples of kRowPad (= 8)
@@ -61,19 +46,19 @@ StoreView store_view(const uspg_ctx *c, int rep)
 // read with evict-first loads (__ldcs) so the image stays in L2 across views.
 // k_forward_finalize turns the sums into ln(P/Pbar) and clears sacc.
 
-template <typename WT>
+template <typename WT, bool MIR>
 __global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict__ idx, const WT *__restrict__ w,
                                                       const uint32_t *__restrict__ grp_ray, long long g0,
                                                       long long n_groups, const float *__restrict__ f,
                                                       const RingEntry *__restrict__ rt, int n_rings, int mG,
-                                                      long long cps, float *__restrict__ sacc)
+                                                      long long cps, float *__restrict__ sacc, Mirror M)
 {
     extern __shared__ int4 tab[];
     fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
     __syncthreads();
-    fwd_groups<WT>(idx, w, grp_ray, g0, n_groups, f, tab, cps, sacc,
-                   ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((long long)gridDim.x * blockDim.x) >> 5,
-                   threadIdx.x & 31);
+    fwd_groups<WT, MIR>(idx, w, grp_ray, g0, n_groups, f, tab, cps, sacc,
+                        ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                        ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
 }
 
 __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__restrict__ proj, int n_rays, float w_scale,
@@ -83,54 +68,75 @@ __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__rest
     if (ray < n_rays) finalize_ray(sacc, proj, ray, w_scale, out_s, out_res);
 }
 
-// ---- per-view correction: lane-ordered cell-major store --------------------------
-//
-// One warp takes SPW slices (32 cells each).  Lane l of a slice owns the cell
-// of its source lane (lane_desc) and its count n; its t-th ray is at
-// slice_off + 32 t + l for t < n.  All stream loads of the warp's slices are
-// issued before the ray-value gathers, and the image value of each cell is
-// fetched first so that its latency overlaps the stream.
-// Persistent warps, one slice per step: the next slice's descriptor loads are
-// issued before the current slice's gathers.  The slice's widest column is
-// lane 0's (lanes are ordered by count), so the unrolled row loop is sized
-// per slice (warp-uniform) to 2, 4 or 8 rows, with a loop beyond.
-template <typename WT>
-__global__ void __launch_bounds__(256, kBwdMinBlocks) k_backward_sell(const long long *__restrict__ slice_off, long long base,
-                                                       const uint32_t *__restrict__ slice_meta,
-                                                       const uint16_t *__restrict__ lane_desc,
-                                                       const uint32_t *__restrict__ cray, const WT *__restrict__ cw,
-                                                       const float *__restrict__ res, float *__restrict__ f,
-                                                       const RingEntry *__restrict__ rt, int mG, long long cps,
-                                                       long long n_slices, float lambda)
+// z-mirror store: one thread per stored ray finalizes it and its mirror
+__global__ void k_forward_finalize_pairs(float *__restrict__ sacc, const float *__restrict__ proj, Mirror M,
+                                         float w_scale, float *__restrict__ out_s, float *__restrict__ out_res)
 {
-    bwd_slices<WT>(slice_off, base, slice_meta, lane_desc, cray, cw, res, f, rt, mG, cps, n_slices, lambda,
-                   ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((long long)gridDim.x * blockDim.x) >> 5,
-                   threadIdx.x & 31);
+    int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray < M.n_rows) finalize_pair(sacc, proj, ray, M, w_scale, out_s, (float2 *)out_res);
 }
 
-template <typename WT>
-static uspg_status fwd_typed(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s)
+// ---- per-view correction: lane-ordered cell-major store --------------------------
+//
+// Lane l of a slice owns the cell of its source lane (lane_desc) and its
+// count n; its t-th ray is at slice_off + 32 t + l for t < n.  Persistent
+// warps, one slice per step: the next slice's descriptor loads are issued
+// before the current slice's gathers, and the image value of each cell is
+// fetched first so that its latency overlaps the stream.  The slice's widest
+// column is lane 0's (lanes are ordered by count), so the unrolled row loop
+// is sized per slice (warp-uniform) to 2, 4 or 8 rows, with a loop beyond.
+template <typename WT, bool MIR>
+__global__ void __launch_bounds__(256, MIR ? kBwdMinBlocksMirror : kBwdMinBlocks)
+    k_backward_sell(const long long *__restrict__ slice_off, long long base, const uint32_t *__restrict__ slice_meta,
+                    const uint16_t *__restrict__ lane_desc, const uint32_t *__restrict__ cray,
+                    const WT *__restrict__ cw, const float *__restrict__ res, float *__restrict__ f,
+                    const RingEntry *__restrict__ rt, int mG, long long cps, long long n_slices, float lambda,
+                    Mirror M)
 {
-    int rep = c->rep_of_view[view];
-    int mG = c->m_of_view[view] % c->G;
-    const long long *rp = c->d_row_ptr + (long long)rep * c->n_rays;
-    long long g0 = c->h_rep_entry0[rep] / kRowPad, ng = (c->h_rep_entry0[rep + 1] - c->h_rep_entry0[rep]) / kRowPad;
-    (void)rp;
-    const int TB = 256;
+    bwd_slices<WT, MIR>(slice_off, base, slice_meta, lane_desc, cray, cw, res, f, rt, mG, cps, n_slices, lambda,
+                        ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                        ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
+}
+
+static int sm_count()
+{
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// forward ray sums of one view into acc (cleared on entry, cleared again by
+// the finalize), then out_s = sums and out_res = log-ratios (pairs when mirrored)
+template <typename WT>
+static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, float *acc, float *out_s, float *out_res,
+                           const float *proj, cudaStream_t s)
+{
+    int rep = c->rep_of_view[view];
+    int mG = c->m_of_view[view] % c->G;
+    long long g0 = c->h_rep_entry0[rep] / kRowPad, ng = (c->h_rep_entry0[rep + 1] - c->h_rep_entry0[rep]) / kRowPad;
+    const int TB = 256;
     int per_sm = c->fwd_blocks_per_sm > 0 ? c->fwd_blocks_per_sm : 8;
     long long want = (ng + TB - 1) / TB;  // one group per thread
-    long long grid = std::min<long long>(want, (long long)sms * per_sm);
+    long long grid = std::min<long long>(want, (long long)sm_count() * per_sm);
     if (grid < 1) grid = 1;
     size_t smem = sizeof(int4) * c->n_rings;
-    k_forward_flat<WT><<<(unsigned)grid, TB, smem, s>>>(c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, c->d_f,
-                                                        c->d_ring, c->n_rings, mG, c->cells_per_slab, c->d_sacc);
+    if (c->mir.on)
+        k_forward_flat<WT, true><<<(unsigned)grid, TB, smem, s>>>(c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng,
+                                                                  f, c->d_ring, c->n_rings, mG, c->cells_per_slab,
+                                                                  acc, c->mir);
+    else
+        k_forward_flat<WT, false><<<(unsigned)grid, TB, smem, s>>>(c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0,
+                                                                   ng, f, c->d_ring, c->n_rings, mG,
+                                                                   c->cells_per_slab, acc, c->mir);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
-    k_forward_finalize<<<(unsigned)((c->n_rays + 255) / 256), 256, 0, s>>>(
-        c->d_sacc, c->d_proj + (long long)view * c->n_rays, c->n_rays, (float)c->w_scale, out_s, out_res);
+    if (c->mir.on)
+        k_forward_finalize_pairs<<<(unsigned)((c->mir.n_rows + 255) / 256), 256, 0, s>>>(
+            acc, proj, c->mir, (float)c->w_scale, out_s, out_res);
+    else
+        k_forward_finalize<<<(unsigned)((c->n_rays + 255) / 256), 256, 0, s>>>(acc, proj, c->n_rays,
+                                                                               (float)c->w_scale, out_s, out_res);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
     return USPG_OK;
@@ -138,9 +144,10 @@ static uspg_status fwd_typed(uspg_ctx *c, int view, float *out_s, float *out_res
 
 uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s)
 {
-    if (c->dtype == USPG_F16) return fwd_typed<__half>(c, view, out_s, out_res, s);
-    if (c->dtype == USPG_BF16) return fwd_typed<__nv_bfloat16>(c, view, out_s, out_res, s);
-    return fwd_typed<float>(c, view, out_s, out_res, s);
+    const float *proj = c->d_proj + (long long)view * c->n_rays;
+    if (c->dtype == USPG_F16) return fwd_run<__half>(c, view, c->d_f, c->d_sacc, out_s, out_res, proj, s);
+    if (c->dtype == USPG_BF16) return fwd_run<__nv_bfloat16>(c, view, c->d_f, c->d_sacc, out_s, out_res, proj, s);
+    return fwd_run<float>(c, view, c->d_f, c->d_sacc, out_s, out_res, proj, s);
 }
 
 template <typename WT>
@@ -150,17 +157,19 @@ static uspg_status bwd_typed(uspg_ctx *c, int view, float lambda, cudaStream_t s
     int mG = c->m_of_view[view] % c->G;
     const long long S = c->slices_per_rep;
     const int TB = 256;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = c->bwd_blocks_per_sm > 0 ? c->bwd_blocks_per_sm : 8;
+    int per_sm = c->bwd_blocks_per_sm > 0 ? c->bwd_blocks_per_sm : (c->mir.on ? kBwdMinBlocksMirror : kBwdMinBlocks);
     long long want = (S * 32 + TB - 1) / TB;
-    long long grid = std::min<long long>(want, (long long)sms * per_sm);
+    long long grid = std::min<long long>(want, (long long)sm_count() * per_sm);
     if (grid < 1) grid = 1;
     long long base = c->h_sell_base[rep];
-    k_backward_sell<WT><<<(unsigned)grid, TB, 0, s>>>(c->d_slice_off + rep * S, base, c->d_slice_meta + rep * S,
-                                                      c->d_lane_desc + 32 * rep * S, c->d_cm_ray, (const WT *)c->d_cm_w,
-                                                      c->d_res, c->d_f, c->d_ring, mG, c->cells_per_slab, S, lambda);
+    if (c->mir.on)
+        k_backward_sell<WT, true><<<(unsigned)grid, TB, 0, s>>>(
+            c->d_slice_off + rep * S, base, c->d_slice_meta + rep * S, c->d_lane_desc + 32 * rep * S, c->d_cm_ray,
+            (const WT *)c->d_cm_w, c->d_res, c->d_f, c->d_ring, mG, c->cells_per_slab, S, lambda, c->mir);
+    else
+        k_backward_sell<WT, false><<<(unsigned)grid, TB, 0, s>>>(
+            c->d_slice_off + rep * S, base, c->d_slice_meta + rep * S, c->d_lane_desc + 32 * rep * S, c->d_cm_ray,
+            (const WT *)c->d_cm_w, c->d_res, c->d_f, c->d_ring, mG, c->cells_per_slab, S, lambda, c->mir);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
     return USPG_OK;
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
                                                    const uint32_t *__restrict__ idx, const WT *__restrict__ w,
                                                    const float *__restrict__ rowmax_all,
                                                    const int *__restrict__ view_rep, const int *__restrict__ view_mg,
-                                                   int n_views, int n_rays, const float *__restrict__ proj,
+                                                   int n_views, int n_rays, Mirror M, const float *__restrict__ proj,
                                                    float *f_g, long long n_cells, const RingEntry *__restrict__ rt,
                                                    int n_rings, long long cps, int iters, float lambda, int rule,
                                                    float tol, float w_scale, int *sweeps_out)
@@ -228,16 +237,29 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
             int rep = view_rep[k];
             fill_tab(tab, rt, n_rings, view_mg[k], lane, 32);
             __syncwarp();
-            const long long *rp = row_ptr_all + (long long)rep * n_rays;
-            const float *rmax = rowmax_all + (long long)rep * n_rays;
+            const long long *rp = row_ptr_all + (long long)rep * M.n_rows;
+            const float *rmax = rowmax_all + (long long)rep * M.n_rows;
             const float *pk = proj + (long long)k * n_rays;
+            // rays of the upper detector rows of a mirrored store read their
+            // mirror's row with the slab flipped
+            auto row_of = [&](int r) { return M.on && r >= M.n_rows ? mirror_ray(r, M.n_u, M.n_v) : r; };
+            auto cell_of = [&](uint32_t pc, bool flip) {
+                return rot_cell(tab, cps, flip ? flip_slab(pc, M.n_slabs) : pc);
+            };
             RowRegs<WT> cur, nxt;
-            long long cb = rp[0], ce = rp[1];
+            int crow = row_of(0);
+            bool cflip = false;  // ray 0 is stored
+            long long cb = rp[crow], ce = rp[crow + 1];
             seq_load(cur, idx, w, cb, ce, lane);
             for (int ray = 0; ray < n_rays; ray++) {
                 long long nb = ce, ne = ce;
+                int nrow = crow;
+                bool nflip = false;
                 if (ray + 1 < n_rays) {
-                    ne = rp[ray + 2];
+                    nrow = row_of(ray + 1);
+                    nflip = nrow != ray + 1;
+                    nb = rp[nrow];
+                    ne = rp[nrow + 1];
                     seq_load(nxt, idx, w, nb, ne, lane);
                 }
                 if (ce > cb) {
@@ -245,18 +267,18 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
                     long long cell[kSeqChunks];
 #pragma unroll
                     for (int c = 0; c < kSeqChunks; c++) {
-                        cell[c] = rot_cell(tab, cps, cur.ix[c]);
+                        cell[c] = cell_of(cur.ix[c], cflip);
                         acc = fmaf(cur.w[c], fs[cell[c]], acc);
                     }
                     for (long long q = cb + kSeqChunks * 32 + lane; q < ce; q += 32)  // long rows
-                        acc = fmaf(load_w1(w, q), fs[rot_cell(tab, cps, __ldg(idx + q))], acc);
+                        acc = fmaf(load_w1(w, q), fs[cell_of(__ldg(idx + q), cflip)], acc);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                     float s = acc * w_scale;
                     if (s > 0.0f) {
                         float ratio = pk[ray] / s;
                         float l2 = log2f(ratio);
-                        float ex = lambda / rmax[ray];
+                        float ex = lambda / rmax[crow];
                         float lin = 1.0f - lambda * (1.0f - ratio);
 #pragma unroll
                         for (int c = 0; c < kSeqChunks; c++) {
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
                         for (long long q = cb + kSeqChunks * 32 + lane; q < ce; q += 32) {
                             float wv = load_w1(w, q);
                             if (wv > 0.0f) {
-                                long long cl = rot_cell(tab, cps, __ldg(idx + q));
+                                long long cl = cell_of(__ldg(idx + q), cflip);
                                 float old = fs[cl];
                                 float fac = rule == USPG_LINEAR_EQ18 ? lin : exp2f(ex * wv * l2);
                                 float nv = old * fac;
@@ -286,6 +308,8 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
                 cur = nxt;
                 cb = nb;
                 ce = ne;
+                crow = nrow;
+                cflip = nflip;
             }
             __syncwarp();
         }
@@ -327,12 +351,14 @@ static uspg_status seq_typed(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t 
         size_t sm = f_bytes + tab_bytes;
         USPG_CUDA(c, cudaFuncSetAttribute(k_sequential<WT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_sequential<WT, true><<<1, 32, sm, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v, d_v + nv,
-                                                 nv, c->n_rays, c->d_proj, c->d_f, c->n_cells, c->d_ring, c->n_rings,
+                                                 nv, c->n_rays, c->mir, c->d_proj, c->d_f, c->n_cells, c->d_ring,
+                                                 c->n_rings,
                                                  c->cells_per_slab, o->iterations, (float)o->lambda, o->update_rule, tol,
                                                  (float)c->w_scale, c->d_sweeps);
     } else {
         k_sequential<WT, false><<<1, 32, tab_bytes, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v,
-                                                         d_v + nv, nv, c->n_rays, c->d_proj, c->d_f, c->n_cells,
+                                                         d_v + nv, nv, c->n_rays, c->mir, c->d_proj, c->d_f,
+                                                         c->n_cells,
                                                          c->d_ring, c->n_rings, c->cells_per_slab, o->iterations,
                                                          (float)o->lambda, o->update_rule, tol, (float)c->w_scale,
                                                          c->d_sweeps);
@@ -389,26 +415,11 @@ static cudaError_t noalloc_acc(float **out)
 template <typename WT>
 static uspg_status fwd_noalloc_typed(uspg_ctx *c, int view, const float *f, float *out, float *acc, cudaStream_t s)
 {
-    int rep = c->rep_of_view[view];
-    int mG = c->m_of_view[view] % c->G;
-    long long g0 = c->h_rep_entry0[rep] / kRowPad, ng = (c->h_rep_entry0[rep + 1] - c->h_rep_entry0[rep]) / kRowPad;
     const int TB = 256;
     k_clear_acc<<<(unsigned)((c->n_rays + TB - 1) / TB), TB, 0, s>>>(acc, c->n_rays);
     launch_counter()++;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = c->fwd_blocks_per_sm > 0 ? c->fwd_blocks_per_sm : 8;
-    long long grid = std::min<long long>((ng + TB - 1) / TB, (long long)sms * per_sm);
-    if (grid < 1) grid = 1;
-    k_forward_flat<WT><<<(unsigned)grid, TB, sizeof(int4) * c->n_rings, s>>>(
-        c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc);
-    launch_counter()++;
-    k_forward_finalize<<<(unsigned)((c->n_rays + TB - 1) / TB), TB, 0, s>>>(acc, c->d_proj, c->n_rays,
-                                                                          (float)c->w_scale, out, nullptr);
-    launch_counter()++;
-    USPG_CUDA(c, cudaGetLastError());
-    return USPG_OK;
+    // sums only (no log-ratios): the projections are not read
+    return fwd_run<WT>(c, view, f, acc, out, nullptr, c->d_proj, s);
 }
 
 }  // namespace uspg

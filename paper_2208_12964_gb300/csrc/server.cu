@@ -213,7 +213,7 @@ int uspg_server::admit(Job *j)
     } else if (found != stores.end()) {  // a new context reading the resident (or building) store
         Store &st = found->second;
         const uspg_ctx *o = st.owner;
-        long long need = 4LL * o->n_cells + 4LL * o->scan.n_views * o->n_rays + 8LL * o->n_rays;
+        long long need = 4LL * o->n_cells + 4LL * o->scan.n_views * o->n_rays + 12LL * o->n_rays;
         if (!make_room(need, j->key) && (!active.empty() || preparing > 0)) {
             mem_wait = true;
             return 0;

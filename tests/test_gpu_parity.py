@@ -52,6 +52,49 @@ def test_rows_3d_cone_small_all_rays(torch_cuda, case):
             assert_rows_equal(gc, gw, oc, ow, TOL_W, where=f"{case} view {k} ray {ray}")
 
 
+@pytest.mark.parametrize("case", ["mirror_odd", "no_mirror"])
+def test_z_mirror_store(torch_cuda, case):
+    """Centred cone scans store only the lower detector rows and the lower
+    and middle slabs of the cell-major store (z-mirror, Sec. III.C symmetry).
+    mirror_odd: odd detector rows and odd slab count, so a detector row and a
+    slab are their own mirrors; no_mirror: an off-centre slab stack, every
+    row stored.  Every row of every view is compared with the oracle's direct
+    trace, the store size with the oracle's counts, and both MART schedules
+    with the oracle."""
+    if case == "mirror_odd":
+        spec = synth.cone_workload(10, 9, 12, 21, iterations=2, lam=0.2, seed=13, noise=False)
+    else:
+        spec = synth.cone_workload(10, 8, 12, 20, iterations=2, lam=0.2, seed=14, noise=False)
+        spec["z_min"] = -0.75  # stack [-0.75, 1.25]: not symmetric about the source plane
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    n_u = n_v = spec["n_u"]
+    st = g.stats()
+    total = 0
+    for k in range(spec["n_views"]):
+        for ray in range(n_u * n_v):
+            gc, gw = g.row(k, ray)
+            oc, ow = o.row(k, ray)
+            assert_rows_equal(gc, gw, oc, ow, TOL_W, where=f"{case} view {k} ray {ray}")
+            total += len(oc)
+    assert total == st["nnz_all_views"]
+    _, rep, _ = o.view_classes()
+    rep_views = [int(np.flatnonzero(rep == q)[0]) for q in range(int(rep.max()) + 1)]
+    full = sum(o.view_nnz(k) for k in rep_views)
+    if case == "mirror_odd":
+        mid = (n_v - 1) // 2
+        self_mirror = sum(len(o.row(k, mid * n_u + u)[0]) for k in rep_views for u in range(n_u))
+        assert st["nnz_store"] == (full + self_mirror) // 2
+    else:
+        assert st["nnz_store"] == full
+    proj = synth.projections(spec)
+    f0 = np.ones(o.n_cells)
+    ref = o.mart_per_view(proj, f0, 2, 0.2)
+    assert rel_l2(_run_mart(g, proj, f0, 2, 0.2, 1), ref) < TOL_IMG
+    ref, _ = o.mart_sequential(proj, f0, 1, 0.2)
+    assert rel_l2(_run_mart(g, proj, f0, 1, 0.2, 0), ref) < TOL_IMG
+
+
 def test_rows_3d_cone_full_size_sampled(torch_cuda):
     """The 128-ring, 128-slab, 90-view, 256x256 workload: 400 sampled rows
     (oracle traces each one directly)."""
