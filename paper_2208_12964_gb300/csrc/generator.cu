@@ -6,20 +6,23 @@
 // and the radial planes of the ring it is in; every piece between two
 // consecutive crossings goes to the cell that holds its midpoint (Eq. 5-10)
 // and pieces shorter than 1e-9 of a cell are dropped.  Unlike a global sort
-// of all crossings, the walk visits the ray ring by ring (ring N-1 inbound,
-// ring N-1 outbound, ring N-2 inbound, ...) and merges only the crossings of
-// one ring segment, so each thread holds O(1) state.  A cell can be entered
-// twice only across the dip into the inner rings, and the walk emits the
-// last inbound and first outbound pieces of a ring back to back, so merging
-// repeated cells needs only the previous entry.
+// of all crossings, the walk follows the ray in path order -- the inbound
+// segments of rings N-1 .. m0, the deepest ring, then the outbound segments
+// m0 .. N-1 -- and merges only the crossings of one ring segment at a time.
+// A cell can be met twice only across the dip into the inner rings; a
+// per-ring record of the cell and position of the ring's last inbound piece
+// merges such repeats.
 //
 // This file is compiled with -fmad=false: the crossings are formed with the
 // same separately rounded operations as their definitions so the index lists
 // do not depend on contraction.
 //
-// Passes: count -> scan -> fill (FP64 weights) -> convert to the stored dtype
-// -> cell-major store (count per cell, slice widths, scan, scatter, per-cell
-// sort by ray id so the layout is deterministic).
+// Passes: size (FP32 bound) -> scan -> fill (FP64 weights) -> convert to the
+// stored dtype -> cell-major store (count per cell, slice widths, scan,
+// scatter, per-cell sort by ray key so the layout is deterministic, lanes
+// ordered by count).  Centred cone scans trace and store only the lower
+// detector rows (z-mirror); the cell-major store then holds the lower and
+// middle slabs, each column serving a cell and its mirror.
 #include "internal.cuh"
 #include "walk.cuh"
 
@@ -46,8 +49,12 @@ __global__ void __launch_bounds__(128) k_size(Geometry g, const RingEntry *rt, c
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_reps * g.n_rows) return;
-    int rep = (int)(gid / g.n_rows), ray = (int)(gid % g.n_rows);
-    caps[gid] = size_ray(g, rt, bdirf, rep_view[rep], ray);
+    // neighbouring threads trace the same ray in different representative
+    // views: rotations about the axis, so the same rings and slabs and nearly
+    // the same sector crossings -- the walks of a warp stay in step
+    int rep = (int)(gid % n_reps), ray = (int)(gid / n_reps);
+    long long row = (long long)rep * g.n_rows + ray;
+    caps[row] = size_ray(g, rt, bdirf, rep_view[rep], ray);
 }
 
 // Exact row lengths (the FP64 walk without storing); used only when a row
@@ -59,14 +66,18 @@ __global__ void __launch_bounds__(128) k_count(Geometry g, const RingEntry *rt, 
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_reps * g.n_rows) return;
-    int rep = (int)(gid / g.n_rows), ray = (int)(gid % g.n_rows);
+    // neighbouring threads trace the same ray in different representative
+    // views: rotations about the axis, so the same rings and slabs and nearly
+    // the same sector crossings -- the walks of a warp stay in step
+    int rep = (int)(gid % n_reps), ray = (int)(gid / n_reps);
+    long long row = (long long)rep * g.n_rows + ray;
     uint32_t in_cell[MAXR];
     double root[MAXR];
     CountSink sink;
     sink.in_cell = in_cell;
     sink.root = root;
     walk_ray(g, rt, bdir, bdirf, rep_view[rep], ray, sink, status);
-    counts[gid] = sink.n;
+    counts[row] = sink.n;
 }
 
 // FP64 walk into the row's slots [row_ptr[i], row_ptr[i+1]); writes the
@@ -79,8 +90,12 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_reps * g.n_rows) return;
-    int rep = (int)(gid / g.n_rows), ray = (int)(gid % g.n_rows);
-    long long b = row_ptr[gid], e = row_ptr[gid + 1];
+    // neighbouring threads trace the same ray in different representative
+    // views: rotations about the axis, so the same rings and slabs and nearly
+    // the same sector crossings -- the walks of a warp stay in step
+    int rep = (int)(gid % n_reps), ray = (int)(gid / n_reps);
+    long long row = (long long)rep * g.n_rows + ray;
+    long long b = row_ptr[row], e = row_ptr[row + 1];
     uint32_t in_cell[MAXR];
     int in_pos[MAXR];
     double root[MAXR];
@@ -93,7 +108,7 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
     sink.in_pos = in_pos;
     walk_ray(g, rt, bdir, bdirf, rep_view[rep], ray, sink, status);
     if (sink.overflow) flag(status, kStatusCountMismatch);
-    counts[gid] = sink.n;
+    counts[row] = sink.n;
     for (long long q = b + sink.n; q < e; q++) {
         idx[q] = 0;
         w64[q] = 0.0;
