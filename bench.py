@@ -258,11 +258,34 @@ def run_ours(args, rank, world, local):
         t_max = float(tt[0])
         if e2e:
             e2e = (float(tt[1]), e2e[1], e2e[2])
-    info = dict(weight_bytes=4 if args.coeff_dtype == "f32" else 2, tuned=tuned, stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
+    info = dict(weight_bytes=4 if args.coeff_dtype == "f32" else 2, coeff_dtype=args.coeff_dtype, tuned=tuned, stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
                 ms_build=ms_build, ms_mart=ms_mart, ms_resample=ms_resample, fw=fw, bw=bw, e2e=e2e, spec=spec,
                 proj=proj_host)
     uspg.uspg_destroy(ctx)
     return info
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_cone128_mart.json")
+
+
+def measured_traffic(kernel: str, dtype: str, mirrored: bool):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
+    None when there is no capture for this form or the kernel sources have
+    changed since it was taken (checked by hash)."""
+    import hashlib
+
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    k = rec["kernels"].get(f"{kernel}/{dtype}/{'mirrored' if mirrored else 'full'}")
+    return k["dram_bytes_per_launch"] if k else None
 
 
 def roofline(info):
@@ -291,7 +314,8 @@ def roofline(info):
     peak, src = load_peaks()
     achieved = b / (t * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "peak_source": src, "traffic": None,
+            "frac": round(achieved / peak, 4), "peak_source": src,
+            "traffic": measured_traffic(name, info.get("coeff_dtype", "f32"), bool(st["mirrored"])),
             "bytes_per_launch": int(b), "ms_per_launch": round(t, 5),
             "other": {"k_forward_ms": round(t_f, 5), "k_backward_ms": round(t_b, 5),
                       "k_forward_GBs": round(fwd_bytes / (t_f * 1e-3) / 1e9, 1),

@@ -359,8 +359,9 @@ int64_t uspg_kernel_launches(void);
  * the forward and of the correction kernel) by timing the candidates on view
  * 0 of this context's own store; the image is saved and restored, so the
  * reconstruction state does not change.  Needs coefficients and projections.
- * choice (optional, host int32[2]) receives {forward blocks per SM,
- * correction blocks per SM}.  Synchronous. */
+ * A candidate replaces a kernel's default shape only when it is at least 5%
+ * faster.  choice (optional, host int32[2]) receives {forward blocks per SM,
+ * correction blocks per SM}, 0 where the default was kept.  Synchronous. */
 uspg_status uspg_autotune(uspg_ctx *ctx, int32_t *choice, uspg_stream stream);
 /* Runs PER_VIEW MART exactly as uspg_mart does, but launches its kernels one
  * by one with a CUDA event between consecutive launches on `stream`, and
