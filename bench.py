@@ -156,7 +156,8 @@ def run_ours(args, rank, world, local):
     ns = spec["n_slabs"]
     img_dev = torch.empty((ns, ny, nx), dtype=torch.float32, device=dev)
     img_pin = torch.empty((ns, ny, nx), dtype=torch.float32).pin_memory()
-    opts, _keep = uspg.mart_opts(iters, lam, uspg.PER_VIEW)
+    seq = spec.get("schedule") == "sequential"  # the paper's ray order (one persistent warp)
+    opts, _keep = uspg.mart_opts(iters, lam, uspg.SEQUENTIAL if seq else uspg.PER_VIEW)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def step_device():
@@ -199,7 +200,7 @@ def run_ours(args, rank, world, local):
         return tot
 
     step_device()
-    tuned = uspg.uspg_autotune(ctx, sp)  # stage ring of the per-view kernels
+    tuned = (0, 0) if seq else uspg.uspg_autotune(ctx, sp)  # launch shape of the per-view kernels
     for _ in range(args.warmup):
         step_device()
     torch.cuda.synchronize(dev)
@@ -236,8 +237,10 @@ def run_ours(args, rank, world, local):
     ms_resample = phase_ms(lambda: uspg.uspg_resample_cartesian(ctx, uspg.RESAMPLE_POINT, nx, ny, img_dev, True, sp))
 
     # per-launch kernel times of the dominant phase
-    uspg.uspg_fill_image(ctx, 1.0, sp)
-    fw, bw = uspg.uspg_mart_kernel_times(ctx, opts, iters * n_views, sp)
+    fw = bw = None
+    if not seq:
+        uspg.uspg_fill_image(ctx, 1.0, sp)
+        fw, bw = uspg.uspg_mart_kernel_times(ctx, opts, iters * n_views, sp)
 
     e2e = None
     if not args.no_e2e:
@@ -265,10 +268,21 @@ def run_ours(args, rank, world, local):
     return info
 
 
+def latency_line(info):
+    """The ray-sequential schedule is a chain of dependent ray steps (each
+    ray's update must land before the next ray's sum): its bound is latency,
+    reported as time per ray step, not as a bandwidth fraction."""
+    st = info["stats"]
+    steps = info["spec"]["iterations"] * st["n_views"] * st["n_rays"]
+    return {"bound": "latency", "kernel": "k_sequential", "achieved": round(info["ms_mart"] * 1e3 / steps, 4),
+            "unit": "us per ray step", "peak": None, "frac": None, "traffic": None,
+            "ray_steps": steps}
+
+
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_cone128_mart.json")
 
 
-def measured_traffic(kernel: str, dtype: str, mirrored: bool):
+def measured_traffic(kernel: str, dtype: str, mirrored: bool, spec: dict):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
     None when there is no capture for this form or the kernel sources have
     changed since it was taken (checked by hash)."""
@@ -284,7 +298,8 @@ def measured_traffic(kernel: str, dtype: str, mirrored: bool):
             h.update(fh.read())
     if h.hexdigest() != rec["sources_sha256"]:
         return None
-    k = rec["kernels"].get(f"{kernel}/{dtype}/{'mirrored' if mirrored else 'full'}")
+    geo = f"{spec['n_rings']}r-{spec['n_slabs'] if spec['geometry'] == 1 else 1}s-{spec['n_u']}x{spec['n_v']}"
+    k = rec["kernels"].get(f"{geo}/{kernel}/{dtype}/{'mirrored' if mirrored else 'full'}")
     return k["dram_bytes_per_launch"] if k else None
 
 
@@ -315,7 +330,7 @@ def roofline(info):
     achieved = b / (t * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": src,
-            "traffic": measured_traffic(name, info.get("coeff_dtype", "f32"), bool(st["mirrored"])),
+            "traffic": measured_traffic(name, info.get("coeff_dtype", "f32"), bool(st["mirrored"]), info["spec"]),
             "bytes_per_launch": int(b), "ms_per_launch": round(t, 5),
             "other": {"k_forward_ms": round(t_f, 5), "k_backward_ms": round(t_b, 5),
                       "k_forward_GBs": round(fwd_bytes / (t_f * 1e-3) / 1e9, 1),
@@ -332,6 +347,14 @@ def oracle_sample(spec, proj, threads=None, n_views=1):
 
     threads = threads or os.cpu_count() or 1
     keys = dict(oracle.Problem._fields_)
+    if spec.get("schedule") == "sequential":  # the whole ray-sequential run, single-threaded
+        o = oracle.Oracle({k: v for k, v in spec.items() if k in keys}, threads=1)
+        f = np.ones(o.n_cells)
+        nnz = spec["iterations"] * sum(o.view_nnz(k) for k in range(spec["n_views"]))
+        t0 = time.perf_counter()
+        o.mart_sequential(proj, f, spec["iterations"], spec["lam"])
+        dt = time.perf_counter() - t0
+        return nnz / dt, 1, dt, nnz
     o = oracle.Oracle({k: v for k, v in spec.items() if k in keys}, threads=threads)
     f = np.ones(o.n_cells)
     t0 = time.perf_counter()
@@ -361,9 +384,11 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": "one per-view MART step (view 0, all 65536 rays)"},
+            "config": {"workload": args.workload,
+                       "sample": ("the whole ray-sequential run" if spec.get("schedule") == "sequential"
+                                  else "one per-view MART step (view 0, all rays)")},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
-                             "sample": f"one per-view MART step of view 0 ({nnz} ray-cell nonzeros) per step"},
+                             "sample": f"{nnz} ray-cell updates per step"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -645,8 +670,11 @@ def main():
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "rings": info["spec"]["n_rings"],
-                       "slabs": info["spec"]["n_slabs"], "views": st["n_views"], "detector": [256, 256],
-                       "iterations": info["spec"]["iterations"], "schedule": "per_view", "coeff_dtype": args.coeff_dtype,
+                       "slabs": info["spec"]["n_slabs"] if info["spec"]["geometry"] == 1 else 1,
+                       "views": st["n_views"],
+                       "detector": [info["spec"]["n_u"], info["spec"]["n_v"] if info["spec"]["geometry"] == 1 else 1],
+                       "iterations": info["spec"]["iterations"], "schedule": info["spec"].get("schedule", "per_view"),
+                       "coeff_dtype": args.coeff_dtype,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}",
                        "step": "coefficient build + MART + resample",
                        "launch_shape": dict(zip(["fwd_blocks_per_sm", "bwd_blocks_per_sm"], info["tuned"]))},
@@ -656,15 +684,16 @@ def main():
             "store": {"reps": st["n_reps"], "nnz_store": st["nnz_store"], "nnz_all_views": st["nnz_all_views"],
                       "store_bytes": st["store_bytes"], "full_matrix_bytes": st["full_matrix_bytes"]},
             "gpu_launches": int(info["launches"]),
-            "clocks": info["clk"], "roofline": roofline(info)}
+            "clocks": info["clk"], "roofline": roofline(info) if info["fw"] is not None else latency_line(info)}
     if info["e2e"]:
         t_e2e, hb, db = info["e2e"]
         line["e2e"] = {"value": info["updates_per_step"] * K * world / (t_e2e * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "ms_per_step": t_e2e / K}
     if not args.no_cpu_baseline and world == 1:
         v, thr, dt, nnz = oracle_sample(info["spec"], info["proj"])
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                "sample": f"one per-view MART step of view 0 ({nnz} nonzeros, {dt:.1f} s)"}
+        what = (f"the whole {info['spec']['iterations']}-iteration ray-sequential run ({nnz} ray-cell updates, "
+                f"{dt:.1f} s)" if info["fw"] is None else f"one per-view MART step of view 0 ({nnz} nonzeros, {dt:.1f} s)")
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": what}
     print(json.dumps(line))
     return 0
 
