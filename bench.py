@@ -56,10 +56,28 @@ def parse():
     ap.add_argument("--coeff-dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve-mixed: mean requests per second")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serve-mixed: arrival window")
-    ap.add_argument("--serve-sustained-seconds", type=float, default=8.0,
+    ap.add_argument("--serve-sustained-seconds", type=float, default=60.0,
                     help="serve-mixed: arrival window of the run at 70%% of capacity")
     ap.add_argument("--serve-active", type=int, default=64, help="serve-mixed: jobs running at once")
     return ap.parse_args()
+
+
+def max_over_ranks(values, device=None):
+    """Element-wise max of per-rank timings over the process group (the
+    slowest rank sets a replica run's time); identity without a group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank reconstructs its own object (independent replicas)."""
+    return base_seed + 1000 * rank
 
 
 def dist_env():
@@ -140,7 +158,7 @@ def run_ours(args, rank, world, local):
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     spec = synth.workload(args.workload)
-    spec["seed"] = spec["seed"] + 1000 * rank  # each replica reconstructs its own object
+    spec["seed"] = replica_seed(spec["seed"], rank)
     proj_host = synth.projections(spec)
     n_views, n_rays = proj_host.shape
     iters, lam = spec["iterations"], spec["lam"]
@@ -254,13 +272,9 @@ def run_ours(args, rank, world, local):
 
     t_max = t_dev
     if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([t_dev, e2e[0] if e2e else 0.0], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt[0])
+        t_max, t_e2e = max_over_ranks([t_dev, e2e[0] if e2e else 0.0], dev)
         if e2e:
-            e2e = (float(tt[1]), e2e[1], e2e[2])
+            e2e = (t_e2e, e2e[1], e2e[2])
     info = dict(weight_bytes=4 if args.coeff_dtype == "f32" else 2, coeff_dtype=args.coeff_dtype, tuned=tuned, stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
                 ms_build=ms_build, ms_mart=ms_mart, ms_resample=ms_resample, fw=fw, bw=bw, e2e=e2e, spec=spec,
                 proj=proj_host)
