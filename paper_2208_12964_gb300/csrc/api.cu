@@ -91,7 +91,7 @@ static void free_store(uspg_ctx *c)
 static uspg_status alloc_state(uspg_ctx *c)
 {
     if (c->d_f) return USPG_OK;
-    USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * c->n_cells));
+    USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * image_floats(c)));
     USPG_CUDA(c, cudaMalloc(&c->d_proj, sizeof(float) * (long long)c->scan.n_views * c->n_rays));
     // per-ray log-ratios; mirrored stores keep them as pairs per stored ray
     USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * std::max<long long>(c->n_rays, 2LL * c->mir.n_rows)));
@@ -167,6 +167,48 @@ uspg_status ctx_share_store(const uspg_ctx *src, uspg_ctx **out)
     }
     *out = c;
     return USPG_OK;
+}
+
+long long image_floats(const uspg_ctx *c)
+{
+    return c->mir.on ? 2 * image_pairs(c->cells_per_slab, c->n_slabs) : c->n_cells;
+}
+
+__global__ void k_to_pairs(const float *__restrict__ f, float2 *__restrict__ fp, long long n_pairs, long long cps,
+                           int n_slabs)
+{
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pairs) return;
+    long long s = k / cps, w = k - s * cps;
+    fp[k] = make_float2(f[k], f[(n_slabs - 1 - s) * cps + w]);
+}
+
+__global__ void k_from_pairs(const float2 *__restrict__ fp, float *__restrict__ f, long long n_pairs, long long cps,
+                             int n_slabs)
+{
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pairs) return;
+    long long s = k / cps, w = k - s * cps;
+    float2 v = fp[k];
+    f[k] = v.x;
+    if (2 * s != n_slabs - 1) f[(n_slabs - 1 - s) * cps + w] = v.y;  // the middle slab holds one cell
+}
+
+cudaError_t image_to_pairs(const uspg_ctx *c, const float *f, float *pairs, cudaStream_t s)
+{
+    long long n = image_pairs(c->cells_per_slab, c->n_slabs);
+    k_to_pairs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, (float2 *)pairs, n, c->cells_per_slab, c->n_slabs);
+    launch_counter()++;
+    return cudaGetLastError();
+}
+
+cudaError_t image_from_pairs(const uspg_ctx *c, const float *pairs, float *f, cudaStream_t s)
+{
+    long long n = image_pairs(c->cells_per_slab, c->n_slabs);
+    k_from_pairs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2 *)pairs, f, n, c->cells_per_slab,
+                                                             c->n_slabs);
+    launch_counter()++;
+    return cudaGetLastError();
 }
 
 long long ctx_device_bytes(const uspg_ctx *c)
@@ -486,8 +528,21 @@ uspg_status uspg_set_image(uspg_ctx *c, const float *f, int32_t on_device, uspg_
     if (!c || !f) return fail(c, USPG_EINVAL, "NULL argument");
     uspg_status st = ensure_state(c);
     if (st) return st;
-    USPG_CUDA(c, cudaMemcpyAsync(c->d_f, f, sizeof(float) * c->n_cells,
-                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->mir.on) {
+        USPG_CUDA(c, cudaMemcpyAsync(c->d_f, f, sizeof(float) * c->n_cells,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        return USPG_OK;
+    }
+    const float *src = f;  // mirrored: stage on the device, then pair up
+    float *tmp = nullptr;
+    if (!on_device) {
+        USPG_CUDA(c, cudaMallocAsync(&tmp, sizeof(float) * c->n_cells, s));
+        USPG_CUDA(c, cudaMemcpyAsync(tmp, f, sizeof(float) * c->n_cells, cudaMemcpyHostToDevice, s));
+        src = tmp;
+    }
+    USPG_CUDA(c, image_to_pairs(c, src, c->d_f, s));
+    if (tmp) USPG_CUDA(c, cudaFreeAsync(tmp, s));
     return USPG_OK;
 }
 
@@ -502,7 +557,8 @@ uspg_status uspg_fill_image(uspg_ctx *c, float value, uspg_stream stream)
     if (!c) return fail(c, USPG_EINVAL, "NULL context");
     uspg_status st = ensure_state(c);
     if (st) return st;
-    k_fill_value<<<(unsigned)((c->n_cells + 255) / 256), 256, 0, (cudaStream_t)stream>>>(c->d_f, c->n_cells, value);
+    long long n = image_floats(c);  // pairs hold the value twice
+    k_fill_value<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(c->d_f, n, value);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
     return USPG_OK;
@@ -513,8 +569,21 @@ uspg_status uspg_get_image(const uspg_ctx *cc, float *f, int32_t to_device, uspg
     uspg_ctx *c = const_cast<uspg_ctx *>(cc);
     if (!c || !f) return fail(c, USPG_EINVAL, "NULL argument");
     if (!c->d_f) return fail(c, USPG_ENOTREADY, "no image");
-    USPG_CUDA(c, cudaMemcpyAsync(f, c->d_f, sizeof(float) * c->n_cells,
-                                 to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->mir.on) {
+        USPG_CUDA(c, cudaMemcpyAsync(f, c->d_f, sizeof(float) * c->n_cells,
+                                     to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        return USPG_OK;
+    }
+    if (to_device) {
+        USPG_CUDA(c, image_from_pairs(c, c->d_f, f, s));
+        return USPG_OK;
+    }
+    float *tmp = nullptr;
+    USPG_CUDA(c, cudaMallocAsync(&tmp, sizeof(float) * c->n_cells, s));
+    USPG_CUDA(c, image_from_pairs(c, c->d_f, tmp, s));
+    USPG_CUDA(c, cudaMemcpyAsync(f, tmp, sizeof(float) * c->n_cells, cudaMemcpyDeviceToHost, s));
+    USPG_CUDA(c, cudaFreeAsync(tmp, s));
     return USPG_OK;
 }
 
@@ -637,8 +706,8 @@ uspg_status uspg_autotune(uspg_ctx *c, int32_t *choice, uspg_stream stream)
     if (!c->have_proj) return fail(c, USPG_ENOTREADY, "projections not set");
     cudaStream_t s = (cudaStream_t)stream;
     float *saved = nullptr;
-    USPG_CUDA(c, cudaMallocAsync(&saved, sizeof(float) * c->n_cells, s));
-    USPG_CUDA(c, cudaMemcpyAsync(saved, c->d_f, sizeof(float) * c->n_cells, cudaMemcpyDeviceToDevice, s));
+    USPG_CUDA(c, cudaMallocAsync(&saved, sizeof(float) * image_floats(c), s));
+    USPG_CUDA(c, cudaMemcpyAsync(saved, c->d_f, sizeof(float) * image_floats(c), cudaMemcpyDeviceToDevice, s));
     cudaEvent_t e0, e1;
     USPG_CUDA(c, cudaEventCreate(&e0));
     USPG_CUDA(c, cudaEventCreate(&e1));
@@ -691,7 +760,7 @@ uspg_status uspg_autotune(uspg_ctx *c, int32_t *choice, uspg_stream stream)
     cudaEventDestroy(e1);
     cudaGetLastError();
     c->err.clear();
-    USPG_CUDA(c, cudaMemcpyAsync(c->d_f, saved, sizeof(float) * c->n_cells, cudaMemcpyDeviceToDevice, s));
+    USPG_CUDA(c, cudaMemcpyAsync(c->d_f, saved, sizeof(float) * image_floats(c), cudaMemcpyDeviceToDevice, s));
     USPG_CUDA(c, cudaFreeAsync(saved, s));
     USPG_CUDA(c, cudaStreamSynchronize(s));
     for (auto &kv : c->graphs) {  // captured launches carry the old configuration

@@ -273,8 +273,9 @@ uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_
     // and restored so the instances' state does not change
     std::vector<float *> saved(n, nullptr);
     for (int i = 0; i < n; i++) {
-        if (cudaMallocAsync(&saved[i], sizeof(float) * ctxs[i]->n_cells, s) != cudaSuccess ||
-            cudaMemcpyAsync(saved[i], ctxs[i]->d_f, sizeof(float) * ctxs[i]->n_cells, cudaMemcpyDeviceToDevice, s) !=
+        if (cudaMallocAsync(&saved[i], sizeof(float) * image_floats(ctxs[i]), s) != cudaSuccess ||
+            cudaMemcpyAsync(saved[i], ctxs[i]->d_f, sizeof(float) * image_floats(ctxs[i]), cudaMemcpyDeviceToDevice,
+                            s) !=
                 cudaSuccess) {
             uspg_batch_destroy(b);
             return fail(nullptr, USPG_ENOMEM, "batch: tuning scratch");
@@ -313,7 +314,7 @@ uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int i = 0; i < n; i++) {
-        cudaMemcpyAsync(ctxs[i]->d_f, saved[i], sizeof(float) * ctxs[i]->n_cells, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(ctxs[i]->d_f, saved[i], sizeof(float) * image_floats(ctxs[i]), cudaMemcpyDeviceToDevice, s);
         cudaFreeAsync(saved[i], s);
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) {

@@ -21,6 +21,15 @@ __device__ __forceinline__ long long rot_cell(const int4 *tab, long long cps, ui
     return (long long)cell_slab(pc) * cps + t.x + s;
 }
 
+// rotated position of a stored entry within its slab (head + sector)
+__device__ __forceinline__ int rot_within(const int4 *tab, uint32_t pc)
+{
+    int4 t = tab[cell_ring(pc)];
+    int s = cell_sector(pc) + t.z;
+    s = s >= t.y ? s - t.y : s;
+    return t.x + s;
+}
+
 __device__ __forceinline__ void fill_tab(int4 *tab, const RingEntry *rt, int n_rings, int mG, int tid, int nt)
 {
     for (int i = tid; i < n_rings; i += nt) {
@@ -102,8 +111,9 @@ __device__ __forceinline__ void load_group(Group8<WT> &G, const uint32_t *idx, c
 // gathers, and lanes of the same ray are combined by a segmented shuffle sum.
 // MIR (z-mirror store): every stored row also yields the sum of its mirror
 // ray, from the same entries with the slab flipped; a row that is its own
-// mirror adds once.
-template <typename WT, bool MIR>
+// mirror adds once.  PAIRS: the image is in the mirrored pair layout, so one
+// 8-byte gather gives a cell and its mirror.
+template <typename WT, bool MIR, bool PAIRS = MIR>
 __device__ __forceinline__ void fwd_groups(const uint32_t *__restrict__ idx, const WT *__restrict__ w,
                                            const uint32_t *__restrict__ grp_ray, long long g0, long long n_groups,
                                            const float *__restrict__ f, const int4 *tab, long long cps,
@@ -119,7 +129,22 @@ __device__ __forceinline__ void fwd_groups(const uint32_t *__restrict__ idx, con
         long long nb = base + step;
         load_group(nxt, idx, w, grp_ray, g0 + nb + lane, nb + lane < n_groups);
         float acc = 0.0f, accm = 0.0f;
-        if (MIR) {
+        if (MIR && PAIRS) {
+            float2 gp[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                int sl = cell_slab(cur.c[i]);
+                int lo = 2 * sl <= M.n_slabs - 1 ? sl : M.n_slabs - 1 - sl;  // pair row: the lower slab
+                long long k = (long long)lo * cps + rot_within(tab, cur.c[i]);
+                gp[i] = cur.w[i] != 0.0f ? __ldg((const float2 *)f + k) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                bool low = 2 * cell_slab(cur.c[i]) <= M.n_slabs - 1;
+                acc = fmaf(cur.w[i], low ? gp[i].x : gp[i].y, acc);
+                accm = fmaf(cur.w[i], low ? gp[i].y : gp[i].x, accm);
+            }
+        } else if (MIR) {
             float gv[8], gm[8];
 #pragma unroll
             for (int i = 0; i < 8; i++) {
@@ -306,11 +331,13 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
         // cell ids are below 2^31 (checked at context creation): 32-bit index math
         int slab = cell_slab(cur.m);
         uint32_t within = (uint32_t)re.head + (uint32_t)s2;
-        float *fp = f + (uint32_t)(slab * (uint32_t)cps + within);
+        uint32_t k = slab * (uint32_t)cps + within;  // MIR: the pair {cell, mirror cell} of the image
+        float *fp = f + k;
         bool pair = MIR && 2 * slab != M.n_slabs - 1;  // the middle slab is its own mirror
-        float *fq = MIR ? f + (uint32_t)((M.n_slabs - 1 - slab) * (uint32_t)cps + within) : fp;
-        float fv = cnt > 0 ? *fp : 0.0f;
-        float fm = (MIR && pair && cnt > 0) ? *fq : 0.0f;
+        float2 fpv = make_float2(0.0f, 0.0f);
+        if (MIR && cnt > 0) fpv = ((const float2 *)f)[k];
+        float fv = MIR ? fpv.x : (cnt > 0 ? *fp : 0.0f);
+        float fm = fpv.y;
         uint32_t off = cur.off + lane;
         load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
         CellSums S{0.f, 0.f, 0.f, 0.f, false, false};
@@ -335,8 +362,13 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
                 }
             }
         }
-        if (S.den > 0.0f) *fp = S.zero ? 0.0f : fv * expf(lambda * (S.num / S.den));
-        if (MIR && pair && S.denm > 0.0f) *fq = S.zerom ? 0.0f : fm * expf(lambda * (S.numm / S.denm));
+        if (MIR) {
+            float nx = S.den > 0.0f ? (S.zero ? 0.0f : fv * expf(lambda * (S.num / S.den))) : fv;
+            float ny = !pair ? nx : (S.denm > 0.0f ? (S.zerom ? 0.0f : fm * expf(lambda * (S.numm / S.denm))) : fm);
+            if (S.den > 0.0f || (pair && S.denm > 0.0f)) ((float2 *)f)[k] = make_float2(nx, ny);
+        } else if (S.den > 0.0f) {
+            *fp = S.zero ? 0.0f : fv * expf(lambda * (S.num / S.den));
+        }
         cur = nxt;
     }
 }

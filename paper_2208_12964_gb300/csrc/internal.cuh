@@ -54,6 +54,15 @@ struct Mirror {
     int n_rows;            // stored rays per view (= n_rays when off)
 };
 
+// A mirrored context keeps its image as pairs {f(slab s), f(slab n_s-1-s)}
+// over the lower and middle slabs: pair k = s * cells_per_slab + c for
+// s < (n_s+1)/2 (the middle slab of an odd stack holds its value twice), so
+// one 8-byte access serves a cell and its mirror.
+__host__ __device__ inline long long image_pairs(long long cells_per_slab, int n_slabs)
+{
+    return (long long)((n_slabs + 1) / 2) * cells_per_slab;
+}
+
 __host__ __device__ inline uint32_t flip_slab(uint32_t pc, int n_slabs)
 {
     return (uint32_t(n_slabs - 1 - cell_slab(pc)) << 22) | (pc & 0x3fffffu);
@@ -202,6 +211,11 @@ uspg_status launch_backward_view(uspg_ctx *c, int view, float lambda, cudaStream
 uspg_status launch_sequential(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s);
 // device bytes currently held by a context (its own buffers only)
 long long ctx_device_bytes(const uspg_ctx *c);
+// floats of the context's image buffer (pairs when mirrored)
+long long image_floats(const uspg_ctx *c);
+// image layout conversions (standard [cells] <-> mirrored pairs) on stream s
+cudaError_t image_to_pairs(const uspg_ctx *c, const float *f, float *pairs, cudaStream_t s);
+cudaError_t image_from_pairs(const uspg_ctx *c, const float *pairs, float *f, cudaStream_t s);
 // a new context on src's grid, scan and built store, with its own image,
 // projections and scratch: one more reconstruction of src's geometry without
 // a second copy of the coefficients

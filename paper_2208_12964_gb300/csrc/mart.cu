@@ -46,7 +46,10 @@ std::atomic<int64_t> &launch_counter()
 // read with evict-first loads (__ldcs) so the image stays in L2 across views.
 // k_forward_finalize turns the sums into ln(P/Pbar) and clears sacc.
 
-template <typename WT, bool MIR>
+// PAIRS: the image is the context's mirrored pair layout; a mirrored store
+// read with a caller's standard-layout image (no-alloc projection) uses
+// MIR without PAIRS.
+template <typename WT, bool MIR, bool PAIRS>
 __global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict__ idx, const WT *__restrict__ w,
                                                       const uint32_t *__restrict__ grp_ray, long long g0,
                                                       long long n_groups, const float *__restrict__ f,
@@ -56,9 +59,9 @@ __global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict
     extern __shared__ int4 tab[];
     fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
     __syncthreads();
-    fwd_groups<WT, MIR>(idx, w, grp_ray, g0, n_groups, f, tab, cps, sacc,
-                        ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                        ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
+    fwd_groups<WT, MIR, PAIRS>(idx, w, grp_ray, g0, n_groups, f, tab, cps, sacc,
+                               ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                               ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
 }
 
 __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__restrict__ proj, int n_rays, float w_scale,
@@ -108,9 +111,11 @@ static int sm_count()
 
 // forward ray sums of one view into acc (cleared on entry, cleared again by
 // the finalize), then out_s = sums and out_res = log-ratios (pairs when mirrored)
+// f_pairs: f is in the context's image layout (pairs when mirrored); false
+// for a caller's standard-layout image
 template <typename WT>
-static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, float *acc, float *out_s, float *out_res,
-                           const float *proj, cudaStream_t s)
+static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, bool f_pairs, float *acc, float *out_s,
+                           float *out_res, const float *proj, cudaStream_t s)
 {
     int rep = c->rep_of_view[view];
     int mG = c->m_of_view[view] % c->G;
@@ -121,14 +126,18 @@ static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, float *acc, fl
     long long grid = std::min<long long>(want, (long long)sm_count() * per_sm);
     if (grid < 1) grid = 1;
     size_t smem = sizeof(int4) * c->n_rings;
-    if (c->mir.on)
-        k_forward_flat<WT, true><<<(unsigned)grid, TB, smem, s>>>(c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng,
-                                                                  f, c->d_ring, c->n_rings, mG, c->cells_per_slab,
-                                                                  acc, c->mir);
+    if (c->mir.on && f_pairs)
+        k_forward_flat<WT, true, true><<<(unsigned)grid, TB, smem, s>>>(
+            c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc,
+            c->mir);
+    else if (c->mir.on)
+        k_forward_flat<WT, true, false><<<(unsigned)grid, TB, smem, s>>>(
+            c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc,
+            c->mir);
     else
-        k_forward_flat<WT, false><<<(unsigned)grid, TB, smem, s>>>(c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0,
-                                                                   ng, f, c->d_ring, c->n_rings, mG,
-                                                                   c->cells_per_slab, acc, c->mir);
+        k_forward_flat<WT, false, false><<<(unsigned)grid, TB, smem, s>>>(
+            c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc,
+            c->mir);
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
     if (c->mir.on)
@@ -145,9 +154,10 @@ static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, float *acc, fl
 uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s)
 {
     const float *proj = c->d_proj + (long long)view * c->n_rays;
-    if (c->dtype == USPG_F16) return fwd_run<__half>(c, view, c->d_f, c->d_sacc, out_s, out_res, proj, s);
-    if (c->dtype == USPG_BF16) return fwd_run<__nv_bfloat16>(c, view, c->d_f, c->d_sacc, out_s, out_res, proj, s);
-    return fwd_run<float>(c, view, c->d_f, c->d_sacc, out_s, out_res, proj, s);
+    if (c->dtype == USPG_F16) return fwd_run<__half>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s);
+    if (c->dtype == USPG_BF16)
+        return fwd_run<__nv_bfloat16>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s);
+    return fwd_run<float>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s);
 }
 
 template <typename WT>
@@ -340,6 +350,11 @@ static uspg_status seq_typed(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t 
     USPG_CUDA(c, cudaMallocAsync(&d_v, sizeof(int) * 2 * nv, s));
     USPG_CUDA(c, cudaMemcpyAsync(d_v, vr.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, s));
     USPG_CUDA(c, cudaMemcpyAsync(d_v + nv, vm.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, s));
+    float *img = c->d_f;  // the sequential kernel works on the standard layout
+    if (c->mir.on) {
+        USPG_CUDA(c, cudaMallocAsync(&img, sizeof(float) * c->n_cells, s));
+        USPG_CUDA(c, image_from_pairs(c, c->d_f, img, s));
+    }
     size_t tab_bytes = sizeof(int4) * c->n_rings;
     size_t f_bytes = sizeof(float) * ((c->n_cells + 3) & ~3LL);
     int dev = 0, max_smem = 0;
@@ -351,13 +366,13 @@ static uspg_status seq_typed(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t 
         size_t sm = f_bytes + tab_bytes;
         USPG_CUDA(c, cudaFuncSetAttribute(k_sequential<WT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_sequential<WT, true><<<1, 32, sm, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v, d_v + nv,
-                                                 nv, c->n_rays, c->mir, c->d_proj, c->d_f, c->n_cells, c->d_ring,
+                                                 nv, c->n_rays, c->mir, c->d_proj, img, c->n_cells, c->d_ring,
                                                  c->n_rings,
                                                  c->cells_per_slab, o->iterations, (float)o->lambda, o->update_rule, tol,
                                                  (float)c->w_scale, c->d_sweeps);
     } else {
         k_sequential<WT, false><<<1, 32, tab_bytes, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v,
-                                                         d_v + nv, nv, c->n_rays, c->mir, c->d_proj, c->d_f,
+                                                         d_v + nv, nv, c->n_rays, c->mir, c->d_proj, img,
                                                          c->n_cells,
                                                          c->d_ring, c->n_rings, c->cells_per_slab, o->iterations,
                                                          (float)o->lambda, o->update_rule, tol, (float)c->w_scale,
@@ -366,6 +381,10 @@ static uspg_status seq_typed(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t 
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
     USPG_CUDA(c, cudaFreeAsync(d_v, s));
+    if (c->mir.on) {
+        USPG_CUDA(c, image_to_pairs(c, img, c->d_f, s));
+        USPG_CUDA(c, cudaFreeAsync(img, s));
+    }
     return USPG_OK;
 }
 
@@ -419,7 +438,7 @@ static uspg_status fwd_noalloc_typed(uspg_ctx *c, int view, const float *f, floa
     k_clear_acc<<<(unsigned)((c->n_rays + TB - 1) / TB), TB, 0, s>>>(acc, c->n_rays);
     launch_counter()++;
     // sums only (no log-ratios): the projections are not read
-    return fwd_run<WT>(c, view, f, acc, out, nullptr, c->d_proj, s);
+    return fwd_run<WT>(c, view, f, false, acc, out, nullptr, c->d_proj, s);
 }
 
 }  // namespace uspg

@@ -77,17 +77,25 @@ uspg_status launch_resample(uspg_ctx *c, int mode, int nx, int ny, float *out, c
 {
     int ns = c->scan.geometry == USPG_CONE_3D ? c->n_slabs : 1;
     const int TB = 256;
+    const float *f = c->d_f;
+    float *tmp = nullptr;
+    if (c->mir.on) {  // mirrored image pairs -> standard layout
+        USPG_CUDA(c, cudaMallocAsync(&tmp, sizeof(float) * c->n_cells, s));
+        USPG_CUDA(c, image_from_pairs(c, c->d_f, tmp, s));
+        f = tmp;
+    }
     if (mode == USPG_RESAMPLE_POINT) {
         long long n = (long long)nx * ny * ns;
-        k_resample_point<<<(unsigned)((n + TB - 1) / TB), TB, 0, s>>>(c->d_f, c->d_ring, c->n_rings, c->r,
+        k_resample_point<<<(unsigned)((n + TB - 1) / TB), TB, 0, s>>>(f, c->d_ring, c->n_rings, c->r,
                                                                       c->cells_per_slab, ns, nx, ny, out);
     } else {
         long long n = 4LL * c->n_rings * c->n_rings * ns;
-        k_resample_bijection<<<(unsigned)((n + TB - 1) / TB), TB, 0, s>>>(c->d_f, c->d_ring, c->n_rings,
+        k_resample_bijection<<<(unsigned)((n + TB - 1) / TB), TB, 0, s>>>(f, c->d_ring, c->n_rings,
                                                                           c->cells_per_slab, ns, out);
     }
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
+    if (tmp) USPG_CUDA(c, cudaFreeAsync(tmp, s));
     return USPG_OK;
 }
 
