@@ -59,13 +59,19 @@ struct Ray {
     // the XY projection (z at the same parameter) and the direction
     float cx, cy, cz, fdx, fdy, fdz;
     float inv_r, inv_h, zmin, Rf, fS, fD;
+    // error bounds of the FP32 estimates (set by ray_setup): midpoint x, y;
+    // and the margins, in units of the floored quantity, inside which a ring
+    // or slab index is left to the exact FP64 rule
+    float exy, mr, mz;
 };
 
-// Margin (in units of the quantity being floored) inside which the FP32
-// estimate of a ring, slab or sector index is not trusted and the exact FP64
-// rule decides.  FP32 estimates here are accurate to ~1e-4 of a unit for
-// grids up to 1024 rings/slabs and 4096 sectors.
-constexpr float kClassMargin = 2e-3f;
+// The FP32 estimate of a ring, slab or sector index is trusted only when
+// its floor lies farther from an integer than twice the estimate's error
+// bound (per ray, from the magnitudes of the FP32 operands; see ray_setup);
+// otherwise the exact FP64 rule decides.  kMaxMargin caps the sector margin
+// (a larger error sends the piece to the exact rule).
+constexpr float kMaxMargin = 0.25f;
+constexpr float kEps32 = 6.0e-8f;  // 2^-24, unit roundoff of FP32
 
 // Repeated cells.  The walk emits pieces in ray order, so the pieces of one
 // cell are adjacent -- except for a cell of ring j that the ray leaves
@@ -164,9 +170,10 @@ USPG_HD inline uint32_t classify_exact(const Geometry &g, const RingEntry *rt, c
 }
 
 // Same decision from an FP32 estimate of the midpoint; returns false when any
-// of the three floors lies within kClassMargin of an integer (or the point is
-// too close to the axis for its azimuth to be trusted), so that the caller
-// takes the exact path.  Where it returns true it agrees with classify_exact.
+// of the three floors lies within twice its error bound of an integer (or the
+// point is too close to the axis for its azimuth to be trusted), so that the
+// caller takes the exact path.  Where it returns true it agrees with
+// classify_exact.
 USPG_HD inline bool classify_fast(const Geometry &g, const RingEntry *rt, const Ray &R, double la, double lb,
                                   uint32_t *out)
 {
@@ -175,26 +182,28 @@ USPG_HD inline bool classify_fast(const Geometry &g, const RingEntry *rt, const 
     float rho = sqrtf(mx * mx + my * my);
     float rr = rho * R.inv_r;
     float fr = floorf(rr);
-    if (rr - fr < kClassMargin || rr - fr > 1.0f - kClassMargin) return false;
+    if (rr - fr < R.mr || rr - fr > 1.0f - R.mr) return false;
     int ring = (int)fr;
     if (ring > g.n_rings - 1) return false;
     int slab = 0;
     if (g.geometry == USPG_CONE_3D) {
         float zz = (R.cz + dl * R.fdz - R.zmin) * R.inv_h;
         float fz = floorf(zz);
-        if (zz - fz < kClassMargin || zz - fz > 1.0f - kClassMargin) return false;
+        if (zz - fz < R.mz || zz - fz > 1.0f - R.mz) return false;
         slab = (int)fz;
         if (slab < 0 || slab > g.n_slabs - 1) return false;
     }
     int ng = rt[ring].ng;
-    // azimuth error: 4e-7 R / rho from the FP32 midpoint, 3e-7 from atan2f
-    float errx = (4e-7f * R.Rf / rho + 3e-7f) * (float)ng * 0.15915494f;
-    if (!(errx < 0.5f * kClassMargin)) return false;  // close to the axis
+    // azimuth error: the midpoint's position error over rho, plus atan2f's
+    // and the scaling's roundoff, in sector units
+    float scale = (float)ng * 0.15915494f;
+    float mphi = 2.0f * ((1.5f * R.exy / rho + 4.0f * kEps32 * 6.2831853f) * scale + 4.0f * kEps32 * (float)ng);
+    if (!(mphi < kMaxMargin)) return false;  // close to the axis
     float phi = atan2f(my, mx);
     if (phi < 0.0f) phi += 6.2831853f;
-    float x = phi * ((float)ng * 0.15915494f);
+    float x = phi * scale;
     float fx = floorf(x);
-    if (x - fx < kClassMargin || x - fx > 1.0f - kClassMargin) return false;
+    if (x - fx < mphi || x - fx > 1.0f - mphi) return false;
     int sec = (int)fx;
     if (sec >= ng) sec -= ng;
     if (sec < 0 || sec >= ng) return false;
@@ -487,6 +496,19 @@ USPG_HD inline bool ray_setup(const Geometry &g, int view, int ray, Ray &R, doub
     R.Rf = (float)Rc;
     R.fS = (float)sqrt(ax * ax + ay * ay);
     R.fD = (float)sqrt(R.a);
+    // FP32 midpoint m = c + dl d (|dl| <= 1): roundoff of c, dl, d, the
+    // product and the sum is below eps (|c| + 3 |d| + |m|) per coordinate;
+    // doubled for the two coordinates and the square root
+    R.exy = 2.0f * kEps32 * (2.0f * R.Rf + 3.0f * R.fD);
+    float err_r = (R.exy + 2.0f * kEps32 * R.Rf) * R.inv_r + 2.0f * kEps32 * (float)N;
+    R.mr = fmaxf(2.0f * err_r, 1e-6f);
+    R.mz = 1e-6f;
+    if (g.geometry == USPG_CONE_3D) {
+        float zext = (float)(fabs(g.z_min) + (double)g.n_slabs * g.h);
+        float err_z = 2.0f * kEps32 * (fabsf(R.cz) + 3.0f * fabsf(R.fdz) + 2.0f * zext) * R.inv_h +
+                      2.0f * kEps32 * (float)g.n_slabs;
+        R.mz = fmaxf(2.0f * err_z, 1e-6f);
+    }
     m0 = (int)floor(R.d / g.r) + 1;
     if (m0 < 1) m0 = 1;
     while (m0 > 1 && (double)(m0 - 1) * g.r > R.d) m0--;
