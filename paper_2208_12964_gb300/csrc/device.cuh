@@ -6,6 +6,15 @@
 
 namespace uspg {
 
+// ---- programmatic dependent launch -------------------------------------------
+//
+// The per-view kernels are launched so that each may start while the one
+// before it on the stream drains (programmatic stream serialization).  Each
+// reads only static data (store, tables) before this wait, and everything
+// the previous kernel wrote after it; without such a launch the wait returns
+// at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ---- weight loads ------------------------------------------------------------
 
 __device__ __forceinline__ float load_w1(const float *w, long long q) { return w[q]; }
@@ -125,6 +134,7 @@ __device__ __forceinline__ void fwd_groups(const uint32_t *__restrict__ idx, con
     if (base >= n_groups) return;
     Group8<WT> cur, nxt;
     load_group(cur, idx, w, grp_ray, g0 + base + lane, base + lane < n_groups);
+    grid_dep_wait();  // the image and the accumulator belong to the previous kernels
     for (; base < n_groups; base += step) {
         long long nb = base + step;
         load_group(nxt, idx, w, grp_ray, g0 + nb + lane, nb + lane < n_groups);
@@ -321,6 +331,7 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
     const WT *cwb = cw + base;
     SliceDesc cur, nxt;
     load_desc(cur, slice_off, base, slice_meta, lane_desc, sl, n_slices, lane);
+    grid_dep_wait();  // the log-ratios and the image belong to the previous kernels
     for (; sl < n_slices; sl += W) {
         int cnt = (int)(cur.d & 2047u);
         int width = __shfl_sync(0xffffffffu, cnt, 0);

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict
 __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__restrict__ proj, int n_rays, float w_scale,
                                    float *__restrict__ out_s, float *__restrict__ out_res)
 {
+    grid_dep_wait();
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
     if (ray < n_rays) finalize_ray(sacc, proj, ray, w_scale, out_s, out_res);
 }
@@ -75,6 +76,7 @@ __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__rest
 __global__ void k_forward_finalize_pairs(float *__restrict__ sacc, const float *__restrict__ proj, Mirror M,
                                          float w_scale, float *__restrict__ out_s, float *__restrict__ out_res)
 {
+    grid_dep_wait();
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
     if (ray < M.n_rows) finalize_pair(sacc, proj, ray, M, w_scale, out_s, (float2 *)out_res);
 }
@@ -99,6 +101,24 @@ __global__ void __launch_bounds__(256, MIR ? kBwdMinBlocksMirror : kBwdMinBlocks
     bwd_slices<WT, MIR>(slice_off, base, slice_meta, lane_desc, cray, cw, res, f, rt, mG, cps, n_slices, lambda,
                         ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                         ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
+}
+
+// Launch with programmatic stream serialization (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 static int sm_count()
@@ -126,28 +146,31 @@ static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, bool f_pairs, 
     long long grid = std::min<long long>(want, (long long)sm_count() * per_sm);
     if (grid < 1) grid = 1;
     size_t smem = sizeof(int4) * c->n_rings;
+    const uint32_t *idx = c->d_idx, *grp = c->d_grp_ray;
+    const WT *w = (const WT *)c->d_w;
+    const RingEntry *rt = c->d_ring;
+    long long cps = c->cells_per_slab;
+    cudaError_t e;
     if (c->mir.on && f_pairs)
-        k_forward_flat<WT, true, true><<<(unsigned)grid, TB, smem, s>>>(
-            c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc,
-            c->mir);
+        e = launch_pdl(k_forward_flat<WT, true, true>, (unsigned)grid, TB, smem, s, idx, w, grp, g0, ng, f, rt,
+                       c->n_rings, mG, cps, acc, c->mir);
     else if (c->mir.on)
-        k_forward_flat<WT, true, false><<<(unsigned)grid, TB, smem, s>>>(
-            c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc,
-            c->mir);
+        e = launch_pdl(k_forward_flat<WT, true, false>, (unsigned)grid, TB, smem, s, idx, w, grp, g0, ng, f, rt,
+                       c->n_rings, mG, cps, acc, c->mir);
     else
-        k_forward_flat<WT, false, false><<<(unsigned)grid, TB, smem, s>>>(
-            c->d_idx, (const WT *)c->d_w, c->d_grp_ray, g0, ng, f, c->d_ring, c->n_rings, mG, c->cells_per_slab, acc,
-            c->mir);
+        e = launch_pdl(k_forward_flat<WT, false, false>, (unsigned)grid, TB, smem, s, idx, w, grp, g0, ng, f, rt,
+                       c->n_rings, mG, cps, acc, c->mir);
     launch_counter()++;
-    USPG_CUDA(c, cudaGetLastError());
+    USPG_CUDA(c, e);
+    float ws = (float)c->w_scale;
     if (c->mir.on)
-        k_forward_finalize_pairs<<<(unsigned)((c->mir.n_rows + 255) / 256), 256, 0, s>>>(
-            acc, proj, c->mir, (float)c->w_scale, out_s, out_res);
+        e = launch_pdl(k_forward_finalize_pairs, (unsigned)((c->mir.n_rows + 255) / 256), 256, 0, s, acc, proj,
+                       c->mir, ws, out_s, out_res);
     else
-        k_forward_finalize<<<(unsigned)((c->n_rays + 255) / 256), 256, 0, s>>>(acc, proj, c->n_rays,
-                                                                               (float)c->w_scale, out_s, out_res);
+        e = launch_pdl(k_forward_finalize, (unsigned)((c->n_rays + 255) / 256), 256, 0, s, acc, proj, c->n_rays, ws,
+                       out_s, out_res);
     launch_counter()++;
-    USPG_CUDA(c, cudaGetLastError());
+    USPG_CUDA(c, e);
     return USPG_OK;
 }
 
@@ -172,16 +195,22 @@ static uspg_status bwd_typed(uspg_ctx *c, int view, float lambda, cudaStream_t s
     long long grid = std::min<long long>(want, (long long)sm_count() * per_sm);
     if (grid < 1) grid = 1;
     long long base = c->h_sell_base[rep];
+    const long long *so = c->d_slice_off + rep * S;
+    const uint32_t *meta = c->d_slice_meta + rep * S;
+    const uint16_t *ld = c->d_lane_desc + 32 * rep * S;
+    const WT *cw = (const WT *)c->d_cm_w;
+    const float *res = c->d_res;
+    cudaError_t e;
     if (c->mir.on)
-        k_backward_sell<WT, true><<<(unsigned)grid, TB, 0, s>>>(
-            c->d_slice_off + rep * S, base, c->d_slice_meta + rep * S, c->d_lane_desc + 32 * rep * S, c->d_cm_ray,
-            (const WT *)c->d_cm_w, c->d_res, c->d_f, c->d_ring, mG, c->cells_per_slab, S, lambda, c->mir);
+        e = launch_pdl(k_backward_sell<WT, true>, (unsigned)grid, TB, 0, s, so, base, meta, ld,
+                       (const uint32_t *)c->d_cm_ray, cw, res, c->d_f, (const RingEntry *)c->d_ring, mG,
+                       c->cells_per_slab, S, lambda, c->mir);
     else
-        k_backward_sell<WT, false><<<(unsigned)grid, TB, 0, s>>>(
-            c->d_slice_off + rep * S, base, c->d_slice_meta + rep * S, c->d_lane_desc + 32 * rep * S, c->d_cm_ray,
-            (const WT *)c->d_cm_w, c->d_res, c->d_f, c->d_ring, mG, c->cells_per_slab, S, lambda, c->mir);
+        e = launch_pdl(k_backward_sell<WT, false>, (unsigned)grid, TB, 0, s, so, base, meta, ld,
+                       (const uint32_t *)c->d_cm_ray, cw, res, c->d_f, (const RingEntry *)c->d_ring, mG,
+                       c->cells_per_slab, S, lambda, c->mir);
     launch_counter()++;
-    USPG_CUDA(c, cudaGetLastError());
+    USPG_CUDA(c, e);
     return USPG_OK;
 }
 
