@@ -1,6 +1,7 @@
 // K5: USPG -> Cartesian resampling for display (Sec. II.B).
 //
-// POINT mode: one thread per output pixel; the pixel centre is classified
+// POINT mode: one thread per pixel of the plane (all slabs share the
+// classification); the pixel centre is classified
 // into (ring, sector) with the same FP64 rule as the coefficient midpoints
 // (ring = floor(rho / r), sector = floor((atan2 + 1e-12) n_g / 2 pi)), so a
 // pixel centre on a radial boundary belongs to the sector that starts there.
@@ -13,20 +14,21 @@
 
 namespace uspg {
 
+// One thread per pixel of the nx x ny plane: the cell under the pixel centre
+// is the same in every slab, so it is classified once and the slabs are
+// copied in a loop (consecutive threads write consecutive pixels).
 __global__ void k_resample_point(const float *__restrict__ f, const RingEntry *__restrict__ rt, int n_rings, double r,
                                  long long cps, int n_slabs, int nx, int ny, float *__restrict__ out)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long per = (long long)nx * ny;
-    if (t >= per * n_slabs) return;
-    int slab = (int)(t / per);
-    long long pix = t % per;
+    if (pix >= per) return;
     int b = (int)(pix / nx), a = (int)(pix % nx);
     double R = (double)n_rings * r;
     double x = -R + ((double)a + 0.5) * (2.0 * R / (double)nx);
     double y = -R + ((double)b + 0.5) * (2.0 * R / (double)ny);
     double rho = sqrt(x * x + y * y);
-    float v = 0.0f;
+    long long cell = -1;
     if (rho < R) {
         long long ring = (long long)floor(rho / r);
         if (ring > n_rings - 1) ring = n_rings - 1;
@@ -35,9 +37,10 @@ __global__ void k_resample_point(const float *__restrict__ f, const RingEntry *_
         if (phi < 0.0) phi += kTwoPi;
         long long sec = (long long)floor(((phi + kNudge) * (double)ng) / kTwoPi);
         if (sec >= ng) sec -= ng;
-        v = f[(long long)slab * cps + rt[ring].head + sec];
+        cell = rt[ring].head + sec;
     }
-    out[t] = v;
+    for (int slab = 0; slab < n_slabs; slab++)
+        out[slab * per + pix] = cell >= 0 ? f[(long long)slab * cps + cell] : 0.0f;
 }
 
 // Position of pixel (a, b) of a 2N x 2N image along its square ring.
@@ -61,16 +64,15 @@ __device__ __forceinline__ void square_ring_index(int a, int b, int N, int *ring
 __global__ void k_resample_bijection(const float *__restrict__ f, const RingEntry *__restrict__ rt, int N,
                                      long long cps, int n_slabs, float *__restrict__ out)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int W = 2 * N;
     long long per = (long long)W * W;
-    if (t >= per * n_slabs) return;
-    int slab = (int)(t / per);
-    long long pix = t % per;
+    if (pix >= per) return;
     int b = (int)(pix / W), a = (int)(pix % W);
     int n, j;
     square_ring_index(a, b, N, &n, &j);
-    out[t] = f[(long long)slab * cps + rt[n - 1].head + j];
+    long long cell = rt[n - 1].head + j;
+    for (int slab = 0; slab < n_slabs; slab++) out[slab * per + pix] = f[(long long)slab * cps + cell];
 }
 
 uspg_status launch_resample(uspg_ctx *c, int mode, int nx, int ny, float *out, cudaStream_t s)
@@ -85,11 +87,11 @@ uspg_status launch_resample(uspg_ctx *c, int mode, int nx, int ny, float *out, c
         f = tmp;
     }
     if (mode == USPG_RESAMPLE_POINT) {
-        long long n = (long long)nx * ny * ns;
+        long long n = (long long)nx * ny;
         k_resample_point<<<(unsigned)((n + TB - 1) / TB), TB, 0, s>>>(f, c->d_ring, c->n_rings, c->r,
                                                                       c->cells_per_slab, ns, nx, ny, out);
     } else {
-        long long n = 4LL * c->n_rings * c->n_rings * ns;
+        long long n = 4LL * c->n_rings * c->n_rings;
         k_resample_bijection<<<(unsigned)((n + TB - 1) / TB), TB, 0, s>>>(f, c->d_ring, c->n_rings,
                                                                           c->cells_per_slab, ns, out);
     }
