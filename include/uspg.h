@@ -241,6 +241,9 @@ void uspg_batch_destroy(uspg_batch *batch);
  *    CUDA-graph launch); every pass of the scheduler issues the next chunk of
  *    each job whose previous chunk has finished, so jobs overlap on the device
  *    and a new job starts without waiting for the running ones to end;
+ *  - priority: a job's stream gets a CUDA stream priority from its size
+ *    (iterations x rays x rings; smaller jobs higher), so short jobs are not
+ *    queued behind a large job's kernels;
  *  - preparation: a second library thread builds the coefficients of a job
  *    whose geometry is not resident and uploads its projections, so neither
  *    stalls the running jobs.

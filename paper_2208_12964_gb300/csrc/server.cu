@@ -10,6 +10,9 @@
 //    pass issues the next chunk of each job whose previous chunk has
 //    completed, so jobs that arrive while others run start at once and their
 //    kernels overlap on the device (continuous batching);
+//  - job streams get a priority by job size (smaller first), and the graphs
+//    of a job run at its stream's priority, so short jobs are not stuck
+//    behind the kernels of a large one;
 //  - the preparer builds the coefficients of an admitted job whose geometry
 //    has no resident store, uploads its projections and sets its initial
 //    image, so that neither a build nor a large copy stalls the running jobs.
@@ -505,7 +508,14 @@ uspg_status uspg_server_submit(uspg_server *s, const uspg_job *job, uint64_t *id
     }
     j->f0 = job->f0;
     j->key = geometry_key(*j);
-    if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess ||
+    // smaller jobs get higher stream priority (graphs run at the priority of
+    // the stream they are launched into), so that their kernels are scheduled
+    // ahead of a large job's when SMs free up: work ~ sweeps x rays x rings
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    double work = (double)job->mart.iterations * (double)n * job->grid.n_rings;
+    int prio = work < 2e9 ? prio_high : (work < 5e10 ? (prio_low + prio_high) / 2 : prio_low);
+    if (cudaStreamCreateWithPriority(&j->stream, cudaStreamNonBlocking, prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess) {
         if (j->stream) cudaStreamDestroy(j->stream);
         delete j;
