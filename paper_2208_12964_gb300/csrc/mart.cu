@@ -141,7 +141,7 @@ static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, bool f_pairs, 
     int mG = c->m_of_view[view] % c->G;
     long long g0 = c->h_rep_entry0[rep] / kRowPad, ng = (c->h_rep_entry0[rep + 1] - c->h_rep_entry0[rep]) / kRowPad;
     const int TB = 256;
-    int per_sm = c->fwd_blocks_per_sm > 0 ? c->fwd_blocks_per_sm : 8;
+    int per_sm = c->fwd_blocks_per_sm > 0 ? c->fwd_blocks_per_sm : 4;  // 4 x 256 threads at 64 registers fill an SM
     long long want = (ng + TB - 1) / TB;  // one group per thread
     long long grid = std::min<long long>(want, (long long)sm_count() * per_sm);
     if (grid < 1) grid = 1;
