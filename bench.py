@@ -175,7 +175,8 @@ def run_ours(args, rank, world, local):
     img_dev = torch.empty((ns, ny, nx), dtype=torch.float32, device=dev)
     img_pin = torch.empty((ns, ny, nx), dtype=torch.float32).pin_memory()
     seq = spec.get("schedule") == "sequential"  # the paper's ray order (one persistent warp)
-    opts, _keep = uspg.mart_opts(iters, lam, uspg.SEQUENTIAL if seq else uspg.PER_VIEW)
+    rule = spec.get("rule", uspg.POWER)  # Table 1's fan scan uses the update of Eq. 18
+    opts, _keep = uspg.mart_opts(iters, lam, uspg.SEQUENTIAL if seq else uspg.PER_VIEW, rule)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def step_device():
@@ -366,7 +367,7 @@ def oracle_sample(spec, proj, threads=None, n_views=1):
         f = np.ones(o.n_cells)
         nnz = spec["iterations"] * sum(o.view_nnz(k) for k in range(spec["n_views"]))
         t0 = time.perf_counter()
-        o.mart_sequential(proj, f, spec["iterations"], spec["lam"])
+        o.mart_sequential(proj, f, spec["iterations"], spec["lam"], rule=spec.get("rule", oracle.POWER))
         dt = time.perf_counter() - t0
         return nnz / dt, 1, dt, nnz
     o = oracle.Oracle({k: v for k, v in spec.items() if k in keys}, threads=threads)
@@ -687,7 +688,10 @@ def main():
                        "slabs": info["spec"]["n_slabs"] if info["spec"]["geometry"] == 1 else 1,
                        "views": st["n_views"],
                        "detector": [info["spec"]["n_u"], info["spec"]["n_v"] if info["spec"]["geometry"] == 1 else 1],
+                       "geometry": ("parallel-2d", "cone-3d", "fan-2d")[info["spec"]["geometry"]],
                        "iterations": info["spec"]["iterations"], "schedule": info["spec"].get("schedule", "per_view"),
+                       "update_rule": "eq18-linear" if info["spec"].get("rule", 0) == 1 else "power",
+                       "lambda": info["spec"]["lam"],
                        "coeff_dtype": args.coeff_dtype,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}",
                        "step": "coefficient build + MART + resample",

@@ -5,7 +5,8 @@
  * Algebraic Algorithm" (arXiv 2208.12964).
  *
  * The calls follow the paper's statement of the problem: a grid (rings,
- * per-ring sectors, axial slabs), a scan (parallel-beam 2D or cone-beam 3D,
+ * per-ring sectors, axial slabs), a scan (parallel-beam 2D, fan-beam 2D or
+ * cone-beam 3D,
  * view angles, detector), coefficients of the lines computed once for the
  * representative views and reused for every other view by rotation, measured
  * projections in, the field function out (Eq. 17-18), and a Cartesian
@@ -57,7 +58,7 @@ typedef enum {
 /* sector rules (Sec. II.A) */
 enum { USPG_SECT_6N = 0, USPG_SECT_4_2N1 = 1, USPG_SECT_CUSTOM = 2 };
 /* scan geometries (Sec. III, Table 1) */
-enum { USPG_PARALLEL_2D = 0, USPG_CONE_3D = 1 };
+enum { USPG_PARALLEL_2D = 0, USPG_CONE_3D = 1, USPG_FAN_2D = 2 };
 /* coefficient models (Sec. III.B) */
 enum { USPG_LENGTH = 0, USPG_BINARY = 1 };
 /* stored coefficient precision */
@@ -95,7 +96,10 @@ typedef struct {
  * rays of view 0 run along +y.  Cone 3D: source at (-src_to_axis, 0, 0), flat
  * detector of n_u x n_v pixels (pitch du, dv) centred at
  * (src_to_det - src_to_axis, 0, 0) with u along +y and v along +z; the set
- * rotates about z. */
+ * rotates about z.  Fan 2D (Table 1, the paper's 2-D phantoms): n_slabs = 1,
+ * n_v = 1, source at (-src_to_axis, 0), line detector of n_u bins of pitch du
+ * centred at (src_to_det - src_to_axis, 0) along +y (bin a at
+ * u = (2a - (n_u-1)) du/2); dv is ignored. */
 typedef struct {
     int32_t geometry;
     int32_t n_views;

@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 SECT_6N, SECT_4_2N1, SECT_CUSTOM = 0, 1, 2
-PARALLEL_2D, CONE_3D = 0, 1
+PARALLEL_2D, CONE_3D, FAN_2D = 0, 1, 2
 LENGTH, BINARY = 0, 1
 POWER, LINEAR_EQ18 = 0, 1
 

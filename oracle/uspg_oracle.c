@@ -59,6 +59,7 @@
 /* geometries */
 #define OR_PARALLEL_2D 0
 #define OR_CONE_3D 1
+#define OR_FAN_2D 2
 /* weight modes */
 #define OR_LENGTH 0
 #define OR_BINARY 1
@@ -127,7 +128,9 @@ void orc_destroy(orc_ctx *c)
 orc_ctx *orc_create(const orc_problem *p)
 {
     if (p->n_rings < 1 || p->n_slabs < 1 || p->r <= 0.0) return NULL;
+    if (p->geometry != OR_PARALLEL_2D && p->geometry != OR_CONE_3D && p->geometry != OR_FAN_2D) return NULL;
     if (p->geometry == OR_CONE_3D && p->h <= 0.0) return NULL;
+    if (p->geometry == OR_FAN_2D && (p->n_v != 1 || !(p->d_so > 0.0) || !(p->d_sd > p->d_so))) return NULL;
     if (p->n_views < 1 || p->n_u < 1 || p->n_v < 1 || p->arc_den < 1) return NULL;
     orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
     c->p = *p;
@@ -202,8 +205,12 @@ static double view_angle(const orc_problem *p, int32_t k)
  *   u*e_u + 2R*e_r.
  * Cone 3D: the source is at (-d_so, 0, 0), the flat detector is centred at
  *   (d_sd - d_so, 0, 0) with e_u = (0,1,0), e_v = (0,0,1); pixel (a, c) with
- *   ray index c*n_u + a.  Both rotate rigidly about z by the view angle
- *   (Sec. III.C, Table 1 places the source on -x and the detector on +x). */
+ *   ray index c*n_u + a.
+ * Fan 2D (Table 1, 2-D phantoms): the source is at (-d_so, 0), the line
+ *   detector is centred at (d_sd - d_so, 0) with e_u = (0,1); bin a sits at
+ *   u = (2a - (B-1)) * du/2 and its ray runs from the source to the bin.
+ * All three rotate rigidly about z by the view angle (Sec. III.C; Table 1
+ * places the source on -x and the detector on +x). */
 static void ray_endpoints(const orc_ctx *c, int32_t k, int32_t ray, double S[3], double D[3])
 {
     const orc_problem *p = &c->p;
@@ -219,6 +226,15 @@ static void ray_endpoints(const orc_ctx *c, int32_t k, int32_t ray, double S[3],
         S[2] = 0.0;
         D[0] = u * eux + L * erx;
         D[1] = u * euy + L * ery;
+        D[2] = 0.0;
+    } else if (p->geometry == OR_FAN_2D) {
+        double u = (double)(2 * ray - (p->n_u - 1)) * (0.5 * p->du);
+        double off = p->d_sd - p->d_so;
+        S[0] = -p->d_so * ct;
+        S[1] = -p->d_so * st;
+        S[2] = 0.0;
+        D[0] = off * ct + u * (-st);
+        D[1] = off * st + u * ct;
         D[2] = 0.0;
     } else {
         int32_t a = ray % p->n_u, cc = ray / p->n_u;

@@ -247,23 +247,23 @@ uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, 
     const uspg_scan_desc &s = *scan;
     if (g.n_rings < 1 || g.n_rings > kMaxRings) return fail(nullptr, USPG_EINVAL, "n_rings must be in [1, 1024]");
     if (!(g.ring_width > 0.0) || !std::isfinite(g.ring_width)) return fail(nullptr, USPG_EINVAL, "ring_width must be > 0");
-    if (s.geometry != USPG_PARALLEL_2D && s.geometry != USPG_CONE_3D)
+    if (s.geometry != USPG_PARALLEL_2D && s.geometry != USPG_CONE_3D && s.geometry != USPG_FAN_2D)
         return fail(nullptr, USPG_EINVAL, "unknown scan geometry");
     int ns = s.geometry == USPG_CONE_3D ? g.n_slabs : 1;
-    if (s.geometry == USPG_PARALLEL_2D && g.n_slabs != 1)
-        return fail(nullptr, USPG_EINVAL, "a parallel 2D scan needs n_slabs = 1");
+    if (s.geometry != USPG_CONE_3D && g.n_slabs != 1)
+        return fail(nullptr, USPG_EINVAL, "a 2D scan needs n_slabs = 1");
     if (ns < 1 || ns > kMaxSlabs) return fail(nullptr, USPG_EINVAL, "n_slabs must be in [1, 1024]");
     if (s.geometry == USPG_CONE_3D && !(g.slab_height > 0.0)) return fail(nullptr, USPG_EINVAL, "slab_height must be > 0");
     if (s.n_views < 1 || s.n_u < 1 || s.n_v < 1 || s.arc_den < 1 || s.arc_num < 0)
         return fail(nullptr, USPG_EINVAL, "n_views, n_u, n_v, arc_den must be >= 1 and arc_num >= 0");
-    if (s.geometry == USPG_PARALLEL_2D && s.n_v != 1) return fail(nullptr, USPG_EINVAL, "parallel 2D scans have n_v = 1");
+    if (s.geometry != USPG_CONE_3D && s.n_v != 1) return fail(nullptr, USPG_EINVAL, "2D scans have n_v = 1");
     if (!(s.du > 0.0) || (s.geometry == USPG_CONE_3D && !(s.dv > 0.0)))
         return fail(nullptr, USPG_EINVAL, "detector pitch must be > 0");
     if ((long long)s.n_u * s.n_v >= (1LL << 31)) return fail(nullptr, USPG_EINVAL, "too many rays per view");
     double R = g.n_rings * g.ring_width;
-    if (s.geometry == USPG_CONE_3D) {
-        if (!(s.src_to_axis > R) || !(s.src_to_det > s.src_to_axis))
-            return fail(nullptr, USPG_EINVAL, "cone scan needs src_to_det > src_to_axis > grid radius");
+    if (s.geometry != USPG_PARALLEL_2D) {
+        if (!(s.src_to_axis > R) || !(s.src_to_det > s.src_to_axis) || !std::isfinite(s.src_to_det))
+            return fail(nullptr, USPG_EINVAL, "cone and fan scans need src_to_det > src_to_axis > grid radius");
         // the detector must see the cylinder: its half-width at the axis must exceed 0
         double half_u = 0.5 * s.n_u * s.du * s.src_to_axis / s.src_to_det;
         if (!(half_u > 0.0)) return fail(nullptr, USPG_EINVAL, "detector misses the object");

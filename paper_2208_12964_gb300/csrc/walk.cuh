@@ -38,6 +38,16 @@ USPG_HD inline void ray_endpoints(const Geometry &g, int k, int ray, double S[3]
         D[0] = u * eux + L * erx;
         D[1] = u * euy + L * ery;
         D[2] = 0.0;
+    } else if (g.geometry == USPG_FAN_2D) {
+        // fan (Table 1): source on -x, line detector on +x, bin along +y
+        double u = (double)(2 * ray - (g.n_u - 1)) * (0.5 * g.du);
+        double off = g.d_sd - g.d_so;
+        S[0] = -g.d_so * ct;
+        S[1] = -g.d_so * st;
+        S[2] = 0.0;
+        D[0] = off * ct + u * (-st);
+        D[1] = off * st + u * ct;
+        D[2] = 0.0;
     } else {
         int a = ray % g.n_u, c = ray / g.n_u;
         double u = (double)(2 * a - (g.n_u - 1)) * (0.5 * g.du);

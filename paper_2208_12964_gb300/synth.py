@@ -15,6 +15,8 @@ Scan conventions (the same ones the library and the oracle state):
   * cone 3D: source (-d_so, 0, 0), detector centre (d_sd - d_so, 0, 0), axes
     e_u = (0,1,0), e_v = (0,0,1), pixel (a, c) at ((2a-(Nu-1)) du/2,
     (2c-(Nv-1)) dv/2), ray index c*Nu + a; the whole set rotates about z.
+  * fan 2D: source (-d_so, 0), line detector centred at (d_sd - d_so, 0)
+    along e_u = (0,1), bin a at u = (2a-(Nu-1)) du/2; rotates about the axis.
 """
 from __future__ import annotations
 
@@ -24,7 +26,8 @@ import re
 import numpy as np
 
 SECT_6N, SECT_4_2N1, SECT_CUSTOM = 0, 1, 2
-PARALLEL_2D, CONE_3D = 0, 1
+PARALLEL_2D, CONE_3D, FAN_2D = 0, 1, 2
+POWER, LINEAR_EQ18 = 0, 1
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -69,6 +72,8 @@ def workload(name: str) -> dict:
         return dict(name=name, n_rings=64, r=1.0 / 64, n_slabs=1, h=1.0, z_min=0.0, sector_rule=SECT_6N,
                     geometry=PARALLEL_2D, n_views=36, arc_num=1, arc_den=2, n_u=65, n_v=1, du=2.0 / 65, dv=1.0,
                     d_so=1.0, d_sd=2.0, iterations=10, lam=0.2, schedule="sequential", seed=1, noise=False)
+    if name == "2d-fan-128r-50v-101":
+        return fan_workload(128, 50, name=name)
     if name == "3d-cone-128r-128s-90v-256":
         return cone_workload(128, 128, 90, 256, iterations=5, lam=0.1, seed=2, name=name)
     if name == "3d-cone-256r-256s-180v-512":
@@ -89,6 +94,22 @@ def cone_workload(rings: int, slabs: int, views: int, det: int, iterations=5, la
                 n_slabs=slabs, h=2.0 / slabs, z_min=-1.0, sector_rule=SECT_6N, geometry=CONE_3D, n_views=views,
                 arc_num=1, arc_den=1, n_u=det, n_v=det, du=2.0 * (8.0 / 3.0) / det, dv=2.0 * (8.0 / 3.0) / det,
                 d_so=4.0, d_sd=8.0, iterations=iterations, lam=lam, schedule="per_view", seed=seed, noise=noise)
+
+
+def fan_workload(rings: int, views: int, bins: int = 101, du: float = 0.05, d_so: float = 8.0, d_sd: float = 16.0,
+                 iterations=10, lam=0.4, seed=5, schedule="sequential", rule=LINEAR_EQ18, name=None) -> dict:
+    """Fan-beam 2D scan of the paper's 2-D phantoms (Table 1): source at
+    (-8, 0), line detector of 101 bins of 0.05 centred at (8, 0), 50 views
+    over a full turn, relaxation 0.4 in the update of Eq. 18, a polar grid
+    with the 4(2n-1) sector rule (rings = half the Cartesian side, so the
+    256 x 256 case is 128 rings).  The object is the unit disk; at the axis
+    the fan spans +-1.26, so every view sees all of it (the outermost bins
+    pass beside the disk).  Table 1 gives no iteration count: 10, as for the
+    parallel workload."""
+    return dict(name=name or f"2d-fan-{rings}r-{views}v-{bins}", n_rings=rings, r=1.0 / rings, n_slabs=1, h=1.0,
+                z_min=0.0, sector_rule=SECT_4_2N1, geometry=FAN_2D, n_views=views, arc_num=1, arc_den=1, n_u=bins,
+                n_v=1, du=du, dv=du, d_so=d_so, d_sd=d_sd, iterations=iterations, lam=lam, schedule=schedule,
+                rule=rule, seed=seed, noise=False)
 
 
 def parallel_workload(rings: int, views: int, bins: int | None = None, arc=(1, 2), seed=1, iterations=10,
@@ -118,6 +139,13 @@ def ray_endpoints(spec: dict, view: int):
         L = 2.0 * R
         S = np.stack([u * ct + L * st, u * st - L * ct, np.zeros_like(u)], axis=1)
         D = np.stack([u * ct - L * st, u * st + L * ct, np.zeros_like(u)], axis=1)
+        return S, D
+    if spec["geometry"] == FAN_2D:
+        a = np.arange(spec["n_u"], dtype=np.float64)
+        u = (2.0 * a - (spec["n_u"] - 1)) * (0.5 * spec["du"])
+        off = spec["d_sd"] - spec["d_so"]
+        S = np.tile(np.array([-spec["d_so"] * ct, -spec["d_so"] * st, 0.0]), (spec["n_u"], 1))
+        D = np.stack([off * ct - u * st, off * st + u * ct, np.zeros_like(u)], axis=1)
         return S, D
     nu, nv = spec["n_u"], spec["n_v"]
     a = np.tile(np.arange(nu, dtype=np.float64), nv)
@@ -281,7 +309,7 @@ def poisson(seed: int, mean: np.ndarray) -> np.ndarray:
 
 def phantom_for(spec: dict):
     R = spec["n_rings"] * spec["r"]
-    if spec["geometry"] == PARALLEL_2D:
+    if spec["geometry"] != CONE_3D:
         return ellipse_phantom(spec["seed"], 6, R)
     zhalf = 0.5 * spec["n_slabs"] * spec["h"]
     return ellipsoid_phantom(spec["seed"], 12, R, zhalf, blob=True)
@@ -292,7 +320,7 @@ def projections(spec: dict, noise: bool | None = None, photons: float = 1e5) -> 
     With noise: counts ~ Poisson(photons * exp(-P)), P~ = ln(photons /
     max(counts, 1)) clamped to >= 0."""
     bodies = phantom_for(spec)
-    planar = spec["geometry"] == PARALLEL_2D
+    planar = spec["geometry"] != CONE_3D
     P = np.zeros((spec["n_views"], n_rays(spec)), np.float64)
     for k in range(spec["n_views"]):
         S, D = ray_endpoints(spec, k)

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libuspg.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EBUSY, ENOTREADY, EDEVICE = range(9)
 SECT_6N, SECT_4_2N1, SECT_CUSTOM = 0, 1, 2
-PARALLEL_2D, CONE_3D = 0, 1
+PARALLEL_2D, CONE_3D, FAN_2D = 0, 1, 2
 LENGTH, BINARY = 0, 1
 F32, F16, BF16 = 0, 1, 2
 SEQUENTIAL, PER_VIEW = 0, 1

@@ -35,6 +35,25 @@ def test_rows_2d_parallel_all_views_all_rays(torch_cuda):
     assert total == st["nnz_all_views"]
 
 
+def test_rows_2d_fan_table1_all_views_all_rays(torch_cuda):
+    """The paper's 2-D fan scan (Table 1): 128 rings of 4(2n-1) sectors,
+    50 views over a full turn, 101 bins of 0.05, source (-8,0), detector
+    (8,0); every row of every view against the oracle's direct trace."""
+    spec = synth.workload("2d-fan-128r-50v-101")
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    st = g.stats()
+    assert st["n_reps"] == 25 and st["n_cells"] == 65536 and st["gcd"] == 4 and not st["mirrored"]
+    total = 0
+    for k in range(50):
+        for a in range(101):
+            gc, gw = g.row(k, a)
+            oc, ow = o.row(k, a)
+            assert_rows_equal(gc, gw, oc, ow, TOL_W, where=f"view {k} bin {a}")
+            total += len(oc)
+    assert total == st["nnz_all_views"]
+
+
 @pytest.mark.parametrize("case", ["6n", "4_2n1", "custom"])
 def test_rows_3d_cone_small_all_rays(torch_cuda, case):
     spec = synth.cone_workload(12, 8, 18, 24, noise=False)
@@ -172,6 +191,26 @@ def test_mart_sequential_2d_workload(torch_cuda):
     got = _run_mart(g, proj, f0, 10, 0.2, 0)
     assert rel_l2(got, ref) < TOL_IMG
     assert np.all(got >= 0)
+
+
+def test_mart_2d_fan_table1(torch_cuda):
+    """Table 1's 2-D reconstruction: ray-sequential MART with the update of
+    Eq. 18 and relaxation 0.4, 10 iterations, f0 = 1; then the per-view
+    schedule (power form) on the same scan."""
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.workload("2d-fan-128r-50v-101")
+    proj = synth.projections(spec)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    f0 = np.ones(o.n_cells)
+    ref, _ = o.mart_sequential(proj, f0, 10, 0.4, rule=1)
+    got = _run_mart(g, proj, f0, 10, 0.4, uspg.SEQUENTIAL, rule=uspg.LINEAR_EQ18)
+    assert rel_l2(got, ref) < TOL_IMG
+    assert np.all(got >= 0)
+    ref = o.mart_per_view(proj, f0, 3, 0.4)
+    got = _run_mart(g, proj, f0, 3, 0.4, uspg.PER_VIEW)
+    assert rel_l2(got, ref) < TOL_IMG
 
 
 @pytest.mark.parametrize("rule", [0, 1])

@@ -29,6 +29,19 @@ def par2d(rings, views=1, bins=3, rule=oracle.SECT_6N, arc=(1, 2), custom=None, 
     return d
 
 
+def fan2d(rings, views, bins, du, rule=oracle.SECT_4_2N1, d_so=8.0, d_sd=16.0):
+    s = synth.fan_workload(rings, views, bins, du, d_so, d_sd)
+    s["sector_rule"] = rule
+    return {k: v for k, v in s.items() if k in dict(oracle.Problem._fields_)}
+
+
+def _fan_axis_distance(u, d_so=8.0, d_sd=16.0):
+    """Distance from the rotation axis of the fan ray through detector
+    offset u: the ray joins (-d_so, 0) to (d_sd - d_so, u), so by similar
+    triangles its distance from the origin is d_so |u| / sqrt(d_sd^2 + u^2)."""
+    return d_so * abs(u) / math.sqrt(d_sd * d_sd + u * u)
+
+
 def cone3d(rings, slabs, views, det, rule=oracle.SECT_6N):
     s = synth.cone_workload(rings, slabs, views, det)
     s["sector_rule"] = rule
@@ -77,6 +90,24 @@ def test_row_sum_is_chord_length_2d():
             u = (2 * b - 64) / 65.0
             assert abs(w.sum() - 2.0 * math.sqrt(1.0 - u * u)) < 1e-12
             assert np.all(np.diff(c) > 0) and np.all(w > 0)
+
+
+def test_row_sum_is_chord_length_2d_fan_table1():
+    """The paper's 2-D fan scan (Table 1: source (-8,0), detector centre
+    (8,0), 101 bins of 0.05, 256 x 256 grid = 128 rings of 4(2n-1) sectors):
+    every ray's weights add up to its chord 2 sqrt(R^2 - d^2) through the unit
+    disk, in every view; the centre bin passes through the axis and the
+    outermost bins pass beside the disk."""
+    spec = fan2d(128, 50, 101, 0.05)
+    o = oracle.Oracle(spec)
+    assert o.n_cells == 256 * 256 and o.G == 4
+    for k in (0, 7, 13, 25, 49):
+        for a in range(101):
+            c, w = o.row(k, a)
+            d = _fan_axis_distance((2 * a - 100) * 0.025)
+            assert abs(w.sum() - 2.0 * math.sqrt(max(1.0 - d * d, 0.0))) < 1e-12, (k, a)
+            assert np.all(np.diff(c) > 0) and np.all(w > 0)
+            assert (len(c) == 0) == (d >= 1.0)  # the outer bins of the fan miss the disk
 
 
 def _cylinder_chord_3d(S, D, R, z0, z1):
@@ -140,7 +171,7 @@ def _brute_force_row(spec, S, D, M=400000):
     return u, cnt * step, step
 
 
-@pytest.mark.parametrize("case", ["6n", "4_2n1", "custom", "3d"])
+@pytest.mark.parametrize("case", ["6n", "4_2n1", "custom", "3d", "fan"])
 def test_row_matches_brute_force_sampling(case):
     # Bin counts are chosen so that no ray passes through the axis (where
     # the sampled azimuth of points exactly on a sector boundary would depend
@@ -152,6 +183,8 @@ def test_row_matches_brute_force_sampling(case):
         spec = par2d(4, views=5, bins=8, rule=oracle.SECT_4_2N1, arc=(1, 1))
     elif case == "custom":
         spec = par2d(3, views=4, bins=6, rule=oracle.SECT_CUSTOM, custom=[3, 7, 5], arc=(1, 1))
+    elif case == "fan":
+        spec = fan2d(3, 5, 8, 0.5)
     else:
         spec = cone3d(3, 3, 3, 8)
     o = oracle.Oracle(spec)
@@ -214,6 +247,22 @@ def test_rotated_rows_equal_direct_rows_3d_cone():
             c, w = o.row(k, ray)
             c2, w2 = o.row_rotated(k, ray)
             assert np.array_equal(c, c2), (k, ray)
+            assert np.allclose(w2, w, rtol=1e-6, atol=0)
+
+
+def test_rotated_rows_equal_direct_rows_2d_fan():
+    """Table 1 fan, 50 views over a full turn on a 4(2n-1) grid (symmetry
+    order 4): 25 representatives, and every view's rows equal the rotated
+    rows of its representative."""
+    spec = fan2d(32, 50, 101, 0.05 * 4)
+    o = oracle.Oracle(spec)
+    n, rep, sh = o.view_classes()
+    assert n == 25
+    for k in range(50):
+        for a in range(101):
+            c, w = o.row(k, a)
+            c2, w2 = o.row_rotated(k, a)
+            assert np.array_equal(c, c2), (k, a)
             assert np.allclose(w2, w, rtol=1e-6, atol=0)
 
 
@@ -395,6 +444,17 @@ def test_synth_disk_projection_closed_form():
         P = synth.line_integrals(disk, S, D, planar=True)
         u = (2 * np.arange(31) - 30) / 31.0
         ref = 2 * np.sqrt(np.maximum(0.36 - u * u, 0))
+        assert np.allclose(P, ref, atol=1e-12)
+
+
+def test_synth_fan_disk_projection_closed_form():
+    disk = [dict(kind="ellipse", dens=1.0, c=(0.0, 0.0, 0.0), axes=(0.6, 0.6, 1.0), rot=np.eye(3))]
+    spec = synth.fan_workload(8, 5)
+    for k in range(5):
+        S, D = synth.ray_endpoints(spec, k)
+        P = synth.line_integrals(disk, S, D, planar=True)
+        d = np.array([_fan_axis_distance((2 * a - 100) * 0.025) for a in range(101)])
+        ref = 2 * np.sqrt(np.maximum(0.36 - d * d, 0))
         assert np.allclose(P, ref, atol=1e-12)
 
 
