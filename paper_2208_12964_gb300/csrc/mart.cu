@@ -248,8 +248,18 @@ __device__ __forceinline__ void seq_load(RowRegs<WT> &R, const uint32_t *idx, co
     }
 }
 
-// One warp.  f in shared memory when SMEM, else in global memory.
-template <typename WT, bool SMEM>
+// Where the sequential kernel keeps the image: in the shared memory of its
+// block when it fits; otherwise its last n_sm cells (the outer rings, which
+// every ray crosses) in shared memory and the inner disk in global memory,
+// which only the rays passing near the axis reach; or, when little of it
+// would fit, all of it in global memory.
+enum { kSeqGlobal = 0, kSeqSmem = 1, kSeqSplit = 2 };
+
+// One warp walks iterations -> views -> rays in order.  Per ray step the
+// rows of the next ray, its projection value and row maximum are already in
+// flight (issued one ray ahead), and the row bounds two rays ahead, so that
+// the chain of a step is the image gathers, the warp sum and the update.
+template <typename WT, int MODE>
 __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__ row_ptr_all,
                                                    const uint32_t *__restrict__ idx, const WT *__restrict__ w,
                                                    const float *__restrict__ rowmax_all,
@@ -257,18 +267,20 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
                                                    int n_views, int n_rays, Mirror M, const float *__restrict__ proj,
                                                    float *f_g, long long n_cells, const RingEntry *__restrict__ rt,
                                                    int n_rings, long long cps, int iters, float lambda, int rule,
-                                                   float tol, float w_scale, int *sweeps_out)
+                                                   float tol, float w_scale, long long n_sm, int *sweeps_out)
 {
     extern __shared__ float4 smem4[];
     float *sm = (float *)smem4;
     const int lane = threadIdx.x;
-    long long fcells = SMEM ? ((n_cells + 3) & ~3LL) : 0;
-    float *fs = SMEM ? sm : f_g;
+    long long fcells = MODE == kSeqSmem ? ((n_cells + 3) & ~3LL) : (MODE == kSeqSplit ? n_sm : 0);
+    // cells [lo, n_cells) live in shared memory at sm[cell - lo]
+    const long long lo = MODE == kSeqSmem ? 0 : (MODE == kSeqSplit ? n_cells - n_sm : n_cells);
     int4 *tab = (int4 *)(sm + fcells);
-    if (SMEM) {
-        for (long long q = lane; q < n_cells; q += 32) fs[q] = f_g[q];
-    }
+    for (long long q = lo + lane; q < n_cells; q += 32) sm[q - lo] = f_g[q];
     __syncwarp();
+    auto F = [&](long long cell) -> float * {
+        return MODE == kSeqSmem ? sm + cell : (MODE == kSeqSplit && cell >= lo ? sm + (cell - lo) : f_g + cell);
+    };
     int it = 0;
     for (; it < iters; it++) {
         int changed = 0;
@@ -286,69 +298,94 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
                 return rot_cell(tab, cps, flip ? flip_slab(pc, M.n_slabs) : pc);
             };
             RowRegs<WT> cur, nxt;
+            // ray 0: rows, projection and row maximum; ray 1: row bounds
             int crow = row_of(0);
             bool cflip = false;  // ray 0 is stored
             long long cb = rp[crow], ce = rp[crow + 1];
+            float cp = pk[0], cmx = rmax[crow];
             seq_load(cur, idx, w, cb, ce, lane);
+            int nrow = crow;
+            bool nflip = false;
+            long long nb = ce, ne = ce;
+            if (n_rays > 1) {
+                nrow = row_of(1);
+                nflip = nrow != 1;
+                nb = rp[nrow];
+                ne = rp[nrow + 1];
+            }
             for (int ray = 0; ray < n_rays; ray++) {
-                long long nb = ce, ne = ce;
-                int nrow = crow;
-                bool nflip = false;
-                if (ray + 1 < n_rays) {
-                    nrow = row_of(ray + 1);
-                    nflip = nrow != ray + 1;
-                    nb = rp[nrow];
-                    ne = rp[nrow + 1];
+                float np = 0.0f, nmx = 1.0f;
+                if (ray + 1 < n_rays) {  // rows and scalars of the next ray
                     seq_load(nxt, idx, w, nb, ne, lane);
+                    np = pk[ray + 1];
+                    nmx = rmax[nrow];
+                }
+                int n2row = nrow;
+                bool n2flip = false;
+                long long n2b = ne, n2e = ne;
+                if (ray + 2 < n_rays) {  // row bounds two rays ahead
+                    n2row = row_of(ray + 2);
+                    n2flip = n2row != ray + 2;
+                    n2b = rp[n2row];
+                    n2e = rp[n2row + 1];
                 }
                 if (ce > cb) {
                     float acc = 0.0f;
                     long long cell[kSeqChunks];
+                    float fv[kSeqChunks];  // each cell occurs once in a row: the update reuses these
 #pragma unroll
                     for (int c = 0; c < kSeqChunks; c++) {
                         cell[c] = cell_of(cur.ix[c], cflip);
-                        acc = fmaf(cur.w[c], fs[cell[c]], acc);
+                        fv[c] = *F(cell[c]);
+                        acc = fmaf(cur.w[c], fv[c], acc);
                     }
                     for (long long q = cb + kSeqChunks * 32 + lane; q < ce; q += 32)  // long rows
-                        acc = fmaf(load_w1(w, q), fs[cell_of(__ldg(idx + q), cflip)], acc);
+                        acc = fmaf(load_w1(w, q), *F(cell_of(__ldg(idx + q), cflip)), acc);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                     float s = acc * w_scale;
                     if (s > 0.0f) {
-                        float ratio = pk[ray] / s;
+                        float ratio = cp / s;
                         float l2 = log2f(ratio);
-                        float ex = lambda / rmax[crow];
+                        float ex = lambda / cmx;
                         float lin = 1.0f - lambda * (1.0f - ratio);
 #pragma unroll
                         for (int c = 0; c < kSeqChunks; c++) {
                             if (cur.w[c] > 0.0f) {
-                                float old = fs[cell[c]];
+                                float old = fv[c];
                                 float fac = rule == USPG_LINEAR_EQ18 ? lin : exp2f(ex * cur.w[c] * l2);
                                 float nv = old * fac;
                                 if (tol > 0.0f && fabsf(nv - old) > tol * fabsf(old)) changed = 1;
-                                fs[cell[c]] = nv;
+                                *F(cell[c]) = nv;
                             }
                         }
                         for (long long q = cb + kSeqChunks * 32 + lane; q < ce; q += 32) {
                             float wv = load_w1(w, q);
                             if (wv > 0.0f) {
-                                long long cl = cell_of(__ldg(idx + q), cflip);
-                                float old = fs[cl];
+                                float *fp = F(cell_of(__ldg(idx + q), cflip));
+                                float old = *fp;
                                 float fac = rule == USPG_LINEAR_EQ18 ? lin : exp2f(ex * wv * l2);
                                 float nv = old * fac;
                                 if (tol > 0.0f && fabsf(nv - old) > tol * fabsf(old)) changed = 1;
-                                fs[cl] = nv;
+                                *fp = nv;
                             }
                         }
                     }
+                    // the next ray may read a cell another lane has just written
+                    if (MODE != kSeqSmem) __threadfence_block();
                     __syncwarp();
-                    if (!SMEM) __threadfence_block();
                 }
                 cur = nxt;
                 cb = nb;
                 ce = ne;
                 crow = nrow;
                 cflip = nflip;
+                cp = np;
+                cmx = nmx;
+                nb = n2b;
+                ne = n2e;
+                nrow = n2row;
+                nflip = n2flip;
             }
             __syncwarp();
         }
@@ -359,11 +396,25 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
             }
         }
     }
-    if (SMEM) {
-        __syncwarp();
-        for (long long q = lane; q < n_cells; q += 32) f_g[q] = fs[q];
-    }
+    __syncwarp();
+    for (long long q = lo + lane; q < n_cells; q += 32) f_g[q] = sm[q - lo];
     if (lane == 0 && sweeps_out) *sweeps_out = it;
+}
+
+template <typename WT, int MODE>
+static cudaError_t seq_launch(uspg_ctx *c, const uspg_mart_opts *o, const int *d_v, float *img, long long n_sm,
+                              size_t smem, cudaStream_t s)
+{
+    auto k = k_sequential<WT, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nv = c->scan.n_views;
+    k<<<1, 32, smem, s>>>((const long long *)c->d_row_ptr, (const uint32_t *)c->d_idx, (const WT *)c->d_w,
+                          (const float *)c->d_rowmax, d_v, d_v + nv, nv, (int)c->n_rays, c->mir,
+                          (const float *)c->d_proj, img, (long long)c->n_cells, (const RingEntry *)c->d_ring,
+                          c->n_rings, (long long)c->cells_per_slab, o->iterations, (float)o->lambda, o->update_rule,
+                          (float)o->stop_tol, (float)c->w_scale, n_sm, c->d_sweeps);
+    return cudaGetLastError();
 }
 
 template <typename WT>
@@ -389,25 +440,18 @@ static uspg_status seq_typed(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t 
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    bool use_smem = f_bytes + tab_bytes <= (size_t)max_smem;
-    float tol = (float)o->stop_tol;
-    if (use_smem) {
-        size_t sm = f_bytes + tab_bytes;
-        USPG_CUDA(c, cudaFuncSetAttribute(k_sequential<WT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_sequential<WT, true><<<1, 32, sm, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v, d_v + nv,
-                                                 nv, c->n_rays, c->mir, c->d_proj, img, c->n_cells, c->d_ring,
-                                                 c->n_rings,
-                                                 c->cells_per_slab, o->iterations, (float)o->lambda, o->update_rule, tol,
-                                                 (float)c->w_scale, c->d_sweeps);
-    } else {
-        k_sequential<WT, false><<<1, 32, tab_bytes, s>>>(c->d_row_ptr, c->d_idx, (const WT *)c->d_w, c->d_rowmax, d_v,
-                                                         d_v + nv, nv, c->n_rays, c->mir, c->d_proj, img,
-                                                         c->n_cells,
-                                                         c->d_ring, c->n_rings, c->cells_per_slab, o->iterations,
-                                                         (float)o->lambda, o->update_rule, tol, (float)c->w_scale,
-                                                         c->d_sweeps);
-    }
+    // cells kept in shared memory by the split form: a multiple of 4, so the
+    // ring table after them stays 16-byte aligned
+    long long n_sm = ((long long)max_smem - (long long)tab_bytes) / (long long)sizeof(float) & ~3LL;
+    cudaError_t e;
+    if (f_bytes + tab_bytes <= (size_t)max_smem)
+        e = seq_launch<WT, kSeqSmem>(c, o, d_v, img, 0, f_bytes + tab_bytes, s);
+    else if (n_sm >= c->n_cells / 8)  // a useful share of the image fits
+        e = seq_launch<WT, kSeqSplit>(c, o, d_v, img, n_sm, sizeof(float) * n_sm + tab_bytes, s);
+    else
+        e = seq_launch<WT, kSeqGlobal>(c, o, d_v, img, 0, tab_bytes, s);
     launch_counter()++;
+    USPG_CUDA(c, e);
     USPG_CUDA(c, cudaGetLastError());
     USPG_CUDA(c, cudaFreeAsync(d_v, s));
     if (c->mir.on) {

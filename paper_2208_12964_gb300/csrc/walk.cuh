@@ -579,6 +579,13 @@ USPG_HD inline int size_segment(const Geometry &g, const RingEntry *rt, const fl
     if (brute) {
         j = 0;
         j_end = ng;
+    } else if (R.sigma == 0.0) {
+        // the ray meets the axis and the segment is radial: the FP64 walk
+        // tests three boundaries around its azimuth (RStream::init), so it
+        // accepts at most three radial crossings here
+        n += 3;
+        j = 0;
+        j_end = 0;
     } else {
         float fa = atan2f(R.cy + da * R.fdy, R.cx + da * R.fdx), fb = atan2f(R.cy + db * R.fdy, R.cx + db * R.fdx);
         if (fa < 0.0f) fa += 6.2831853f;
@@ -589,7 +596,7 @@ USPG_HD inline int size_segment(const Geometry &g, const RingEntry *rt, const fl
         float scale = (float)ng * 0.15915494f;
         j = (long long)floorf(lo_a * scale) - 1;
         j_end = (long long)floorf(hi_a * scale) + 2;
-        if (R.sigma == 0.0 || j_end - j > ng + 3) {
+        if (j_end - j > ng + 3) {
             j = 0;
             j_end = ng;
         }

@@ -213,6 +213,23 @@ def test_mart_2d_fan_table1(torch_cuda):
     assert rel_l2(got, ref) < TOL_IMG
 
 
+@pytest.mark.parametrize("rings,placement", [(90, "shared memory"), (150, "split"), (300, "split"),
+                                           (400, "global memory")])
+def test_mart_sequential_image_placement(torch_cuda, rings, placement):
+    """The ray-sequential kernel keeps the image in its block's shared memory
+    when it fits (6n grid of 24,570 cells), its inner rings in shared memory
+    and the rest in global memory when at least an eighth fits (67,950 and
+    270,900 cells), else all of it in global memory (481,200 cells)."""
+    spec = synth.parallel_workload(rings, 5, 2 * rings + 1, seed=rings)
+    proj = synth.projections(spec)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    f0 = np.ones(o.n_cells)
+    ref, _ = o.mart_sequential(proj, f0, 2, 0.3)
+    got = _run_mart(g, proj, f0, 2, 0.3, 0)
+    assert rel_l2(got, ref) < TOL_IMG, placement
+
+
 @pytest.mark.parametrize("rule", [0, 1])
 def test_mart_sequential_rules_and_stop(torch_cuda, rule):
     from paper_2208_12964_gb300 import uspg
