@@ -253,13 +253,24 @@ __device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_o
     }
 }
 
+// One present entry (weight wt > 0) of a cell: a ray with log-ratio NaN is
+// skipped; -inf (P = 0) zeroes the cell, whatever num becomes.
 __device__ __forceinline__ void acc_entry(float wt, float r, float &num, float &den, bool &zero)
 {
-    bool act = (wt > 0.0f) && (r == r);  // NaN: the ray is skipped
-    bool zr = act && (r == -INFINITY);   // P = 0: the cell is zeroed
-    den += act ? wt : 0.0f;
-    zero |= zr;
-    num += (act && !zr) ? wt * r : 0.0f;
+    if (wt > 0.0f && r == r) {
+        zero |= r == -INFINITY;
+        num = fmaf(wt, r, num);
+        den += wt;
+    }
+}
+
+// f * exp(lambda * num / den) of a cell hit by at least one ray (den > 0),
+// 0 if one of its rays has P = 0.  The ratio is a weighted mean of
+// log-ratios, so the fast reciprocal and exponential (a few units in the
+// last place) are far inside the image tolerance.
+__device__ __forceinline__ float cell_update(float fv, float num, float den, bool zero, float lambda)
+{
+    return zero ? 0.0f : fv * __expf(lambda * __fdividef(num, den));
 }
 
 // Per-lane correction sums of one cell (and, MIR, of its mirror cell).
@@ -374,11 +385,11 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
             }
         }
         if (MIR) {
-            float nx = S.den > 0.0f ? (S.zero ? 0.0f : fv * expf(lambda * (S.num / S.den))) : fv;
-            float ny = !pair ? nx : (S.denm > 0.0f ? (S.zerom ? 0.0f : fm * expf(lambda * (S.numm / S.denm))) : fm);
+            float nx = S.den > 0.0f ? cell_update(fv, S.num, S.den, S.zero, lambda) : fv;
+            float ny = !pair ? nx : (S.denm > 0.0f ? cell_update(fm, S.numm, S.denm, S.zerom, lambda) : fm);
             if (S.den > 0.0f || (pair && S.denm > 0.0f)) ((float2 *)f)[k] = make_float2(nx, ny);
         } else if (S.den > 0.0f) {
-            *fp = S.zero ? 0.0f : fv * expf(lambda * (S.num / S.den));
+            *fp = cell_update(fv, S.num, S.den, S.zero, lambda);
         }
         cur = nxt;
     }
