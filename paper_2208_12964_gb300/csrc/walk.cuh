@@ -232,10 +232,14 @@ USPG_HD inline void piece(const Geometry &g, const RingEntry *rt, const Ray &R, 
     sink.emit(cell, len);
 }
 
-// Axial-plane crossings inside (sa, sb), in ascending parameter order.
+// Axial-plane crossings of the whole ray, in ascending parameter order.  The
+// candidates are the planes between the slabs of the ray's clipped ends, one
+// extra on each side against the rounding of the floors; the ring segments
+// come in ascending order and each takes the candidates strictly inside it,
+// so every plane's parameter is formed once per ray.
 struct ZStream {
     int s, s_end, step;  // candidate plane indices
-    double next;
+    double next;         // parameter of the current candidate (2 when none is left)
     USPG_HD void init(const Geometry &g, const Ray &R, double sa, double sb)
     {
         next = 2.0;
@@ -263,7 +267,8 @@ struct ZStream {
             s_end = 0;
         }
     }
-    USPG_HD void advance(const Geometry &g, const Ray &R, double sa, double sb)
+    // the next candidate plane (interior planes 1 .. n_slabs-1 only)
+    USPG_HD void advance(const Geometry &g, const Ray &R)
     {
         next = 2.0;
         while (s != s_end) {
@@ -271,11 +276,8 @@ struct ZStream {
             s += step;
             if (cs < 1 || cs > g.n_slabs - 1) continue;
             double zs = g.z_min + (double)cs * g.h;
-            double l = (zs - R.S[2]) / R.dz;
-            if (l > sa && l < sb) {
-                next = l;
-                return;
-            }
+            next = (zs - R.S[2]) / R.dz;
+            return;
         }
     }
 };
@@ -369,12 +371,10 @@ struct RStream {
 // Walk the ring-i segment [sa, sb] (already clipped) and emit its pieces.
 template <class Sink>
 USPG_HD void walk_segment(const Geometry &g, const RingEntry *rt, const double2 *bdir, const float2 *bdirf, const Ray &R, int ring,
-                             double sa, double sb, Sink &sink, int *status)
+                             double sa, double sb, ZStream &zs, Sink &sink, int *status)
 {
     if (!(sb > sa)) return;
-    ZStream zs;
-    zs.init(g, R, sa, sb);
-    zs.advance(g, R, sa, sb);
+    while (zs.next <= sa) zs.advance(g, R);  // planes of earlier segments, or on their common end
     double prev = sa;
     if (ring == 0) {
         // all sectors of ring 0 meet on the axis: test every boundary and the
@@ -420,7 +420,7 @@ USPG_HD void walk_segment(const Geometry &g, const RingEntry *rt, const double2 
                 prev = nxt;
             }
             if (rn <= zs.next) q++;
-            else zs.advance(g, R, sa, sb);
+            else zs.advance(g, R);
         }
     } else {
         RStream rs;
@@ -434,7 +434,7 @@ USPG_HD void walk_segment(const Geometry &g, const RingEntry *rt, const double2 
                 prev = nxt;
             }
             if (rs.next <= zs.next) rs.advance(R, bdir, bdirf, sa, sb);
-            else zs.advance(g, R, sa, sb);
+            else zs.advance(g, R);
         }
     }
     if (sb > prev) piece(g, rt, R, prev, sb, sink);
@@ -540,6 +540,9 @@ USPG_HD void walk_ray(const Geometry &g, const RingEntry *rt, const double2 *bdi
     // m0 .. N-1 outbound.
     for (int i = 0; i < N; i++) sink.in_cell[i] = 0xffffffffu;
     sink.outbound = false;
+    ZStream zs;  // the segments below come in ascending parameter order
+    zs.init(g, R, lo, hi);
+    zs.advance(g, R);
     // each circle's root is formed once: the inbound half keeps it (in the
     // sink's per-ring scratch) for the outbound half
     double kout = kR;
@@ -547,18 +550,18 @@ USPG_HD void walk_ray(const Geometry &g, const RingEntry *rt, const double2 *bdi
         double kin = root_k((double)i, g.r, R.d, R.a);
         sink.root[i] = kin;
         double a1 = R.t - kout, b1 = R.t - kin;
-        walk_segment(g, rt, bdir, bdirf, R, i, a1 > lo ? a1 : lo, b1 < hi ? b1 : hi, sink, status);
+        walk_segment(g, rt, bdir, bdirf, R, i, a1 > lo ? a1 : lo, b1 < hi ? b1 : hi, zs, sink, status);
         kout = kin;
     }
     int i0 = m0 - 1;
     double a0 = R.t - kout, b0 = R.t + kout;
-    walk_segment(g, rt, bdir, bdirf, R, i0, a0 > lo ? a0 : lo, b0 < hi ? b0 : hi, sink, status);
+    walk_segment(g, rt, bdir, bdirf, R, i0, a0 > lo ? a0 : lo, b0 < hi ? b0 : hi, zs, sink, status);
     sink.outbound = true;
     double kin = kout;
     for (int i = m0; i <= N - 1; i++) {
         double ko = (i == N - 1) ? kR : sink.root[i + 1];
         double a2 = R.t + kin, b2 = R.t + ko;
-        walk_segment(g, rt, bdir, bdirf, R, i, a2 > lo ? a2 : lo, b2 < hi ? b2 : hi, sink, status);
+        walk_segment(g, rt, bdir, bdirf, R, i, a2 > lo ? a2 : lo, b2 < hi ? b2 : hi, zs, sink, status);
         kin = ko;
     }
 }
