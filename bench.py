@@ -276,7 +276,14 @@ def run_ours(args, rank, world, local):
         t_max, t_e2e = max_over_ranks([t_dev, e2e[0] if e2e else 0.0], dev)
         if e2e:
             e2e = (t_e2e, e2e[1], e2e[2])
-    info = dict(weight_bytes=4 if args.coeff_dtype == "f32" else 2, coeff_dtype=args.coeff_dtype, tuned=tuned, stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
+    # image quality of the final reconstruction against its phantom (Table 2's measures)
+    torch.cuda.synchronize(dev)
+    quality_rep = None
+    if rank == 0:
+        from paper_2208_12964_gb300 import quality
+
+        quality_rep = quality.report(spec, img_dev.cpu().numpy())
+    info = dict(quality=quality_rep, weight_bytes=4 if args.coeff_dtype == "f32" else 2, coeff_dtype=args.coeff_dtype, tuned=tuned, stats=st, t_ms=t_max, updates_per_step=updates_per_step, launches=launches, clk=clk.summary(),
                 ms_build=ms_build, ms_mart=ms_mart, ms_resample=ms_resample, fw=fw, bw=bw, e2e=e2e, spec=spec,
                 proj=proj_host)
     uspg.uspg_destroy(ctx)
@@ -707,6 +714,11 @@ def main():
         t_e2e, hb, db = info["e2e"]
         line["e2e"] = {"value": info["updates_per_step"] * K * world / (t_e2e * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "ms_per_step": t_e2e / K}
+    if info.get("quality"):
+        q = info["quality"]
+        line["quality"] = {"mae": round(q["mae"], 5), "rmse": round(q["rmse"], 5), "ssim": round(q["ssim"], 4),
+                           "vs": "seeded phantom at the resampled image's pixel centres (MAE/RMSE inside the disk)",
+                           "pixels": q["pixels"], "phantom_range": round(q["phantom_range"], 4)}
     if not args.no_cpu_baseline and world == 1:
         v, thr, dt, nnz = oracle_sample(info["spec"], info["proj"])
         what = (f"the whole {info['spec']['iterations']}-iteration ray-sequential run ({nnz} ray-cell updates, "
