@@ -28,6 +28,7 @@ SECT_6N, SECT_4_2N1, SECT_CUSTOM = 0, 1, 2
 PARALLEL_2D, CONE_3D, FAN_2D = 0, 1, 2
 LENGTH, BINARY = 0, 1
 POWER, LINEAR_EQ18 = 0, 1
+STORE_ROWS, STORE_SEGMENTS = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -52,6 +53,7 @@ class Problem(C.Structure):
         ("arc_num", C.c_int64), ("arc_den", C.c_int64),
         ("du", C.c_double), ("dv", C.c_double), ("d_so", C.c_double), ("d_sd", C.c_double),
         ("custom_sectors", C.c_void_p),
+        ("store_form", C.c_int32),
     ]
 
 
@@ -74,9 +76,13 @@ def _load():
                 getattr(L, n).argtypes = [V]
             L.orc_grid_tables.restype = C.c_int32
             L.orc_grid_tables.argtypes = [V, V, V]
-            for n in ("orc_trace", "orc_trace_rotated"):
+            for n in ("orc_trace", "orc_trace_rotated", "orc_rebin_row"):
                 getattr(L, n).restype = C.c_int32
                 getattr(L, n).argtypes = [V, C.c_int32, C.c_int32, C.c_int32, V, V]
+            L.orc_segments.restype = C.c_int32
+            L.orc_segments.argtypes = [V, C.c_int32, C.c_int32, V, V, V, V, V, V]
+            L.orc_view_turns.restype = C.c_uint64
+            L.orc_view_turns.argtypes = [V, C.c_int32]
             L.orc_view_classes.restype = C.c_int32
             L.orc_view_classes.argtypes = [V, V, V]
             L.orc_view_nnz.restype = C.c_int64
@@ -111,7 +117,7 @@ class Oracle:
         self._keep = None
         d = dict(n_rings=1, n_slabs=1, sector_rule=SECT_6N, geometry=PARALLEL_2D, r=1.0, h=1.0, z_min=0.0,
                  n_views=1, n_u=1, n_v=1, weight_mode=LENGTH, arc_num=1, arc_den=2, du=1.0, dv=1.0,
-                 d_so=1.0, d_sd=2.0)
+                 d_so=1.0, d_sd=2.0, store_form=STORE_ROWS)
         d.update({k: v for k, v in spec.items() if k != "custom_sectors"})
         p = Problem(**{k: d[k] for k, _ in Problem._fields_ if k != "custom_sectors"})
         if spec.get("custom_sectors") is not None:
@@ -162,6 +168,27 @@ class Oracle:
     def row_rotated(self, view: int, ray: int):
         """Row rebuilt from the view's representative by sector rotation."""
         return self._row(self.L.orc_trace_rotated, view, ray)
+
+    def rebin_row(self, view: int, ray: int):
+        """Binary row of a view from the first view's segments (Algorithm 1)."""
+        return self._row(self.L.orc_rebin_row, view, ray)
+
+    def segments(self, ray: int):
+        """Segments of a first-view ray: (ring, slab, azimuth in, azimuth out
+        (uint64 fixed turns), length, direction of turn)."""
+        cap = 2 * self.spec["n_rings"] + self.spec["n_slabs"] + 8
+        rg = np.zeros(cap, np.int32)
+        sb = np.zeros(cap, np.int32)
+        fa = np.zeros(cap, np.uint64)
+        fb = np.zeros(cap, np.uint64)
+        ln = np.zeros(cap, np.float64)
+        dr = np.zeros(1, np.int32)
+        n = self.L.orc_segments(self._h, int(ray), cap, _ptr(rg), _ptr(sb), _ptr(fa), _ptr(fb), _ptr(ln), _ptr(dr))
+        assert n >= 0
+        return rg[:n], sb[:n], fa[:n], fb[:n], ln[:n], int(dr[0])
+
+    def view_turns(self, view: int) -> int:
+        return int(self.L.orc_view_turns(self._h, int(view)))
 
     def view_classes(self):
         rep = np.zeros(self.n_views, np.int32)

@@ -74,6 +74,7 @@ typedef struct {
     int64_t arc_num, arc_den;
     double du, dv, d_so, d_sd;
     const int32_t *custom_sectors;
+    int32_t store_form; /* 0: rows traced per view; 1: view-0 segments re-binned per view (binary) */
 } orc_problem;
 
 typedef struct {
@@ -131,6 +132,7 @@ orc_ctx *orc_create(const orc_problem *p)
     if (p->geometry != OR_PARALLEL_2D && p->geometry != OR_CONE_3D && p->geometry != OR_FAN_2D) return NULL;
     if (p->geometry == OR_CONE_3D && p->h <= 0.0) return NULL;
     if (p->geometry == OR_FAN_2D && (p->n_v != 1 || !(p->d_so > 0.0) || !(p->d_sd > p->d_so))) return NULL;
+    if (p->store_form != 0 && (p->store_form != 1 || p->weight_mode != OR_BINARY)) return NULL;
     if (p->n_views < 1 || p->n_u < 1 || p->n_v < 1 || p->arc_den < 1) return NULL;
     orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
     c->p = *p;
@@ -261,6 +263,12 @@ typedef struct {
 static int cmp_double(const void *a, const void *b)
 {
     double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
     return (x > y) - (x < y);
 }
 
@@ -443,9 +451,272 @@ int32_t orc_trace(const orc_ctx *c, int32_t k, int32_t ray, int32_t cap, int64_t
     return (int32_t)n;
 }
 
+/* ------------------------------------------ view-0 segment store (binary) --- */
+
+/* The paper's own store (Sec. III.B-C, Algorithm 1).  With binary
+ * coefficients a line needs only its crossings with the cylinders (Eq. 3-4)
+ * and the axial planes: between two consecutive crossings it stays in one
+ * ring and one slice (Eq. 5-7 at the midpoint), and its cells there are the
+ * sectors between the sectors of the segment's two end points (Eq. 8-16).
+ * Only the segments of the first view are stored -- ring, slice and the
+ * azimuths of the two end points -- and a view at source angle theta adds
+ * theta to every stored azimuth.
+ *
+ * Azimuths are fixed-point turns, 2^64 to the turn, so that adding a view's
+ * angle is exact modular arithmetic and the sector of azimuth F in a ring of
+ * n_g sectors is floor(F n_g / 2^64).  Readings where the paper is silent:
+ *   (1) a line whose closest approach to the axis lies inside ring 0 is cut
+ *       there too (its azimuth turns by up to half a turn around it);
+ *   (2) segments shorter than the piece threshold are dropped;
+ *   (3) an end point on a sector boundary belongs to the sector the segment
+ *       occupies next to it, and an end azimuth within 2^-40 turn of a
+ *       boundary counts as on it, so that rounding noise in the azimuth of a
+ *       crossing that lies on a boundary decides nothing; a segment of a line
+ *       through the axis keeps one azimuth (taken at its midpoint) and the
+ *       counter-clockwise nudge decides a boundary, as for pieces;
+ *   (4) a cell that two segments share (the two halves of a ring around the
+ *       line's dip, or the two sides of the ring-0 cut) is one active cell;
+ *   (5) rounding cannot reverse a segment: an end azimuth that lies behind
+ *       the start in the direction of turn is moved onto the start.
+ * Pieces at a segment's end that are shorter than the threshold are dropped
+ * by the direct trace but counted here: the two forms differ only where a
+ * sector boundary passes within 1e-9 of a cell of a crossing. */
+
+static uint64_t fixed_turns(double phi) /* phi in [0, 2 pi) */
+{
+    double t = phi / OR_TWO_PI;
+    if (!(t >= 0.0) || t >= 1.0) t = 0.0;
+    return (uint64_t)(t * 18446744073709551616.0);
+}
+
+static uint64_t azimuth_fixed(double x, double y)
+{
+    double phi = atan2(y, x);
+    if (phi < 0.0) phi += OR_TWO_PI;
+    return fixed_turns(phi);
+}
+
+/* Source angle of view k in fixed-point turns, floor(k arc 2^64 / p), exact. */
+uint64_t orc_view_turns(const orc_ctx *c, int32_t k)
+{
+    const orc_problem *p = &c->p;
+    int64_t den = p->arc_den * (int64_t)p->n_views;
+    int64_t num = ((int64_t)k * p->arc_num) % den;
+    return (uint64_t)((((unsigned __int128)num) << 64) / (unsigned __int128)den);
+}
+
+#define OR_SNAP_TURNS_LOG2 24 /* 2^24 fixed units = 2^-40 turn */
+
+static int64_t sector_at(uint64_t F, int32_t ng) /* floor(F n_g / 2^64), lines through the axis */
+{
+    return (int64_t)(((unsigned __int128)F * (uint64_t)ng) >> 64);
+}
+
+/* Sector of an end azimuth F of a segment whose azimuth turns in direction
+ * dir (+1 / -1); `start` tells which end.  The sector is floor(F n_g / 2^64)
+ * unless F lies on (or within 2^-40 turn of) a boundary: then the one the
+ * segment occupies next to that boundary. */
+static int64_t end_sector(uint64_t F, int32_t ng, int dir, int start)
+{
+    unsigned __int128 prod = (unsigned __int128)F * (uint64_t)ng;
+    int64_t j = (int64_t)(prod >> 64);
+    uint64_t frac = (uint64_t)prod; /* position inside sector j, 2^-64 units */
+    uint64_t tau = ((uint64_t)ng) << OR_SNAP_TURNS_LOG2;
+    int below = frac < tau;         /* on boundary j */
+    int above = frac > ~tau;        /* on boundary j+1 */
+    int up = (dir > 0) == (start != 0); /* the segment lies above the boundary */
+    if (below && !up) j -= 1;
+    if (above && up) j += 1;
+    j %= ng;
+    return j < 0 ? j + ng : j;
+}
+
+/* First sector (*ja) and number of further sectors of a segment with end
+ * azimuths A -> B turning in direction dir.  A segment narrower than twice
+ * the boundary window has one cell, the sector of its start. */
+static int64_t seg_span(uint64_t A, uint64_t B, int32_t ng, int dir, int64_t *ja_out)
+{
+    int64_t ja = end_sector(A, ng, dir, 1);
+    if (ja_out) *ja_out = ja;
+    uint64_t ext = dir > 0 ? B - A : A - B;
+    if (ext < (2ull << OR_SNAP_TURNS_LOG2)) return 0;
+    int64_t jb = end_sector(B, ng, dir, 0);
+    int64_t span = dir > 0 ? jb - ja : ja - jb;
+    return span < 0 ? span + ng : span;
+}
+
+/* Segments of ray `ray` of the first view, in path order: ring, slice, end
+ * azimuths (fixed turns) and length; *dir = +1 / -1 when the azimuth grows /
+ * falls along the line, 0 for a line through the axis.  Returns the count,
+ * or -(needed) if `cap` is too small. */
+int32_t orc_segments(const orc_ctx *c, int32_t ray, int32_t cap, int32_t *ring, int32_t *slab, uint64_t *fa,
+                     uint64_t *fb, double *len, int32_t *dir)
+{
+    const orc_problem *p = &c->p;
+    *dir = 0;
+    if (ray < 0 || ray >= c->n_rays) return 0;
+    const int N = p->n_rings;
+    const double r = p->r;
+    const double R = (double)N * r;
+    const int is3d = p->geometry == OR_CONE_3D;
+    double S[3], D[3];
+    ray_endpoints(c, 0, ray, S, D);
+    double dx = D[0] - S[0], dy = D[1] - S[1], dz = D[2] - S[2];
+    double L = sqrt(dx * dx + dy * dy + dz * dz);
+    double unit = r;
+    if (is3d && p->h < unit) unit = p->h;
+    const double min_len = OR_MIN_PIECE * unit;
+    double ax = S[0], ay = S[1];
+    double a = dx * dx + dy * dy;
+    if (a == 0.0) return 0;
+    double t = -(ax * dx + ay * dy) / a;
+    double d2 = (ax * ax + ay * ay) - t * t * a;
+    if (d2 < 0.0) d2 = 0.0;
+    double d = sqrt(d2);
+    if (!(d < R)) return 0;
+    double kR = sqrt(((R - d) * (R + d)) / a);
+    double lo = t - kR, hi = t + kR;
+    if (lo < 0.0) lo = 0.0;
+    if (hi > 1.0) hi = 1.0;
+    if (is3d) {
+        double z0 = p->z_min, z1 = p->z_min + (double)p->n_slabs * p->h;
+        if (dz == 0.0) {
+            if (!(S[2] > z0 && S[2] < z1)) return 0;
+        } else {
+            double l0 = (z0 - S[2]) / dz, l1 = (z1 - S[2]) / dz;
+            if (l0 > l1) {
+                double tmp = l0;
+                l0 = l1;
+                l1 = tmp;
+            }
+            if (l0 > lo) lo = l0;
+            if (l1 < hi) hi = l1;
+        }
+    }
+    if (!(hi > lo)) return 0;
+    dbuf X = {0, 0, 0};
+    dpush(&X, lo);
+    dpush(&X, hi);
+    for (int m = 1; m < N; m++) { /* cylinders, Eq. 4 */
+        double rm = (double)m * r;
+        if (!(rm > d)) continue;
+        double km = sqrt(((rm - d) * (rm + d)) / a);
+        double l1 = t - km, l2 = t + km;
+        if (l1 > lo && l1 < hi) dpush(&X, l1);
+        if (l2 > lo && l2 < hi) dpush(&X, l2);
+    }
+    if (is3d && dz != 0.0) { /* axial planes */
+        for (int sl = 1; sl < p->n_slabs; sl++) {
+            double zs = p->z_min + (double)sl * p->h;
+            double l = (zs - S[2]) / dz;
+            if (l > lo && l < hi) dpush(&X, l);
+        }
+    }
+    if (d < r && t > lo && t < hi) dpush(&X, t); /* reading (1) */
+    qsort(X.lam, X.n, sizeof(double), cmp_double);
+    double sigma = ax * dy - ay * dx;
+    *dir = sigma > 0.0 ? 1 : (sigma < 0.0 ? -1 : 0);
+    int32_t n = 0;
+    for (int64_t q = 0; q + 1 < X.n; q++) {
+        double la = X.lam[q], lb = X.lam[q + 1];
+        double ln = (lb - la) * L;
+        if (!(ln >= min_len)) continue; /* reading (2) */
+        double pax = S[0] + la * dx, pay = S[1] + la * dy, paz = S[2] + la * dz;
+        double pbx = S[0] + lb * dx, pby = S[1] + lb * dy, pbz = S[2] + lb * dz;
+        double mx = 0.5 * (pax + pbx), my = 0.5 * (pay + pby), mz = 0.5 * (paz + pbz);
+        int64_t rg = (int64_t)floor(sqrt(mx * mx + my * my) / r); /* Eq. 7 */
+        if (rg < 0) rg = 0;
+        if (rg > N - 1) rg = N - 1;
+        int64_t sb = 0;
+        if (is3d) { /* Eq. 6 */
+            sb = (int64_t)floor((mz - p->z_min) / p->h);
+            if (sb < 0) sb = 0;
+            if (sb > p->n_slabs - 1) sb = p->n_slabs - 1;
+        }
+        if (n < cap) {
+            ring[n] = (int32_t)rg;
+            slab[n] = (int32_t)sb;
+            len[n] = ln;
+            if (*dir == 0) { /* reading (3): one azimuth */
+                fa[n] = fb[n] = azimuth_fixed(mx, my);
+            } else {         /* Eq. 8 at both end points */
+                fa[n] = azimuth_fixed(pax, pay);
+                fb[n] = azimuth_fixed(pbx, pby);
+                if ((int64_t)(fb[n] - fa[n]) * *dir < 0) fb[n] = fa[n]; /* reading (5) */
+            }
+        }
+        n++;
+    }
+    free(X.lam);
+    return n <= cap ? n : -n;
+}
+
+/* Cells of ray `ray` in view k from the first view's segments (the view loop
+ * of Algorithm 1): ascending, unique, weight 1.  Returns the count, or
+ * -(needed) if `cap` is too small. */
+int32_t orc_rebin_row(const orc_ctx *c, int32_t k, int32_t ray, int32_t cap, int64_t *cells, double *w)
+{
+    const orc_problem *p = &c->p;
+    if (k < 0 || k >= p->n_views) return 0;
+    int32_t scap = 2 * p->n_rings + p->n_slabs + 8;
+    int32_t *rg = (int32_t *)malloc(sizeof(int32_t) * scap), *sb = (int32_t *)malloc(sizeof(int32_t) * scap);
+    uint64_t *fa = (uint64_t *)malloc(sizeof(uint64_t) * scap), *fb = (uint64_t *)malloc(sizeof(uint64_t) * scap);
+    double *ln = (double *)malloc(sizeof(double) * scap);
+    int32_t dir = 0;
+    int32_t ns = orc_segments(c, ray, scap, rg, sb, fa, fb, ln, &dir);
+    if (ns < 0) ns = 0; /* cannot happen: at most 2N + slabs + 2 segments */
+    uint64_t T = orc_view_turns(c, k), nudge = fixed_turns(OR_NUDGE);
+    int64_t total = 0;
+    for (int32_t q = 0; q < ns; q++) { /* cells per segment */
+        int32_t ng = c->ng[rg[q]];
+        if (dir == 0) {
+            total += 1;
+        } else {
+            total += seg_span(fa[q] + T, fb[q] + T, ng, dir, NULL) + 1;
+        }
+    }
+    int64_t *all = (int64_t *)malloc(sizeof(int64_t) * (total ? total : 1));
+    int64_t n = 0;
+    for (int32_t q = 0; q < ns; q++) {
+        int32_t ng = c->ng[rg[q]];
+        int64_t base = (int64_t)sb[q] * c->cells_slab + c->head[rg[q]];
+        if (dir == 0) {
+            all[n++] = base + sector_at(fa[q] + T + nudge, ng);
+            continue;
+        }
+        int64_t ja;
+        int64_t span = seg_span(fa[q] + T, fb[q] + T, ng, dir, &ja);
+        for (int64_t i = 0; i <= span; i++) {
+            int64_t j = ja + dir * i;
+            j %= ng;
+            if (j < 0) j += ng;
+            all[n++] = base + j;
+        }
+    }
+    free(rg);
+    free(sb);
+    free(fa);
+    free(fb);
+    free(ln);
+    qsort(all, n, sizeof(int64_t), cmp_i64);
+    int64_t u = 0; /* reading (4) */
+    for (int64_t q = 0; q < n; q++)
+        if (u == 0 || all[q] != all[u - 1]) all[u++] = all[q];
+    if (u > cap) {
+        free(all);
+        return (int32_t)-u;
+    }
+    for (int64_t q = 0; q < u; q++) {
+        cells[q] = all[q];
+        w[q] = 1.0;
+    }
+    free(all);
+    return (int32_t)u;
+}
+
 /* --------------------------------------------- view classes and rotation --- */
 
-/* Rotational reuse of stored rows (Sec. III.B-C, Algorithm 1 steps 18-25).
+/* Rotational reuse of stored rows (Sec. III.B-C, the view loop of Algorithm 1).
  * The grid maps onto itself under a rotation by 1/G turn, G = gcd of the
  * sector counts, which moves every ring by n_g/G sectors.  View k at
  * theta_k = k*arc/p turns is written theta_k = m_k/G + rho_k with
@@ -548,7 +819,7 @@ static int rows_build(const orc_ctx *c, int32_t k, orc_rows *R)
         for (;;) {
             int64_t *cl = (int64_t *)malloc(sizeof(int64_t) * cap);
             double *wl = (double *)malloc(sizeof(double) * cap);
-            int32_t n = orc_trace(c, k, i, cap, cl, wl);
+            int32_t n = c->p.store_form == 1 ? orc_rebin_row(c, k, i, cap, cl, wl) : orc_trace(c, k, i, cap, cl, wl);
             if (n >= 0) {
                 cnt[i] = n;
                 cc[i] = cl;

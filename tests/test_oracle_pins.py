@@ -466,3 +466,78 @@ def test_synth_poisson_moments_and_determinism():
     lo, hi = a[:20000], a[20000:]
     assert abs(lo.mean() - 3.0) < 0.05 and abs(lo.var() - 3.0) < 0.15
     assert abs(hi.mean() - 2500.0) < 1.5 and abs(hi.var() / 2500.0 - 1) < 0.05
+
+
+# ------------------------------------------- view-0 segment store (binary) ---
+
+def _binary(spec, store_form=oracle.STORE_ROWS):
+    d = {k: v for k, v in spec.items() if k in dict(oracle.Problem._fields_)}
+    d["weight_mode"] = oracle.BINARY
+    d["store_form"] = store_form
+    return oracle.Oracle(d)
+
+
+@pytest.mark.parametrize("case", ["parallel64", "fan128", "cone12_6n", "cone12_4n"])
+def test_segment_store_rows_equal_direct_binary_rows(case):
+    """Algorithm 1: the first view's segments (cylinder and axial-plane
+    crossings, ring, slice, end azimuths), turned by each view's source angle
+    and re-binned to sectors, give every view's binary row exactly as the
+    direct trace of that view does -- including the centre rays through the
+    axis and the crossings that lie on a sector boundary."""
+    if case == "parallel64":
+        spec = synth.workload("2d-parallel-64r-36v")
+    elif case == "fan128":
+        spec = synth.workload("2d-fan-128r-50v-101")
+    else:
+        spec = synth.cone_workload(12, 8, 18, 24, noise=False)
+        spec["sector_rule"] = oracle.SECT_6N if case == "cone12_6n" else oracle.SECT_4_2N1
+    o = _binary(spec)
+    for k in range(spec["n_views"]):
+        for ray in range(o.n_rays):
+            c, w = o.row(k, ray)
+            c2, w2 = o.rebin_row(k, ray)
+            assert np.array_equal(c, c2), (case, k, ray)
+            assert np.all(w2 == 1.0)
+
+
+def test_segment_lengths_sum_to_chord_and_counts():
+    """The segments of a first-view ray tile its chord (closed form), each
+    lies in one ring; a ray has at most 2N + slabs + 1 segments."""
+    spec = synth.workload("2d-fan-128r-50v-101")
+    o = _binary(spec)
+    for a in range(101):
+        rg, sb, fa, fb, ln, dr = o.segments(a)
+        d = _fan_axis_distance((2 * a - 100) * 0.025)
+        assert abs(ln.sum() - 2.0 * math.sqrt(max(1.0 - d * d, 0.0))) < 1e-12
+        assert len(rg) <= 2 * 128 + 1 + 1
+        if len(rg):  # the centre bin passes through the axis; the outermost bins miss the disk
+            assert dr == (0 if a == 50 else (1 if a < 50 else -1))
+    spec3 = cone3d(8, 6, 5, 16)
+    o3 = _binary(spec3)
+    S, D = synth.ray_endpoints(spec3, 0)
+    for ray in range(0, o3.n_rays, 7):
+        rg, sb, fa, fb, ln, dr = o3.segments(ray)
+        assert abs(ln.sum() - _cylinder_chord_3d(S[ray], D[ray], 1.0, -1.0, 1.0)) < 1e-12
+        assert len(rg) <= 2 * 8 + 6 + 1
+
+
+def test_view_turns_are_exact_fixed_point():
+    o = _binary(synth.workload("2d-fan-128r-50v-101"))
+    for k in range(50):
+        assert o.view_turns(k) == (k * (1 << 64)) // 50
+    o2 = _binary(synth.workload("2d-parallel-64r-36v"))
+    for k in range(36):
+        assert o2.view_turns(k) == (k * (1 << 64)) // 72  # half a turn over 36 views
+
+
+def test_segment_store_mart_equals_direct_binary_mart():
+    """Sequential MART (Eq. 18) over the re-binned rows equals MART over the
+    directly traced binary rows (same rows, same order)."""
+    spec = synth.fan_workload(32, 12, 41, 0.1)
+    proj = synth.projections(spec)
+    o = _binary(spec)
+    os_ = _binary(spec, oracle.STORE_SEGMENTS)
+    f0 = np.ones(o.n_cells)
+    a, _ = o.mart_sequential(proj, f0, 3, 0.4, rule=oracle.LINEAR_EQ18)
+    b, _ = os_.mart_sequential(proj, f0, 3, 0.4, rule=oracle.LINEAR_EQ18)
+    assert np.array_equal(a, b)
