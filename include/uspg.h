@@ -61,6 +61,17 @@ enum { USPG_SECT_6N = 0, USPG_SECT_4_2N1 = 1, USPG_SECT_CUSTOM = 2 };
 enum { USPG_PARALLEL_2D = 0, USPG_CONE_3D = 1, USPG_FAN_2D = 2 };
 /* coefficient models (Sec. III.B) */
 enum { USPG_LENGTH = 0, USPG_BINARY = 1 };
+/* coefficient stores (Sec. III.B-C):
+ *  REPRESENTATIVES  rows of one representative view per class of views that
+ *                   differ by a rotation of the grid (length or binary
+ *                   weights; every schedule);
+ *  SEGMENTS         the paper's store for binary weights (Algorithm 1): the
+ *                   first view's segments between cylinder and axial-plane
+ *                   crossings (ring, slab, azimuths of the two ends); every
+ *                   view's cells are enumerated from them on the fly by adding
+ *                   its source angle.  One store for all views, whatever their
+ *                   angles; the ray-sequential schedule. */
+enum { USPG_STORE_REPRESENTATIVES = 0, USPG_STORE_SEGMENTS = 1 };
 /* stored coefficient precision */
 enum { USPG_F32 = 0, USPG_F16 = 1, USPG_BF16 = 2 };
 /* MART schedules (Sec. III.D) */
@@ -112,7 +123,8 @@ typedef struct {
 typedef struct {
     int32_t weight_mode; /* USPG_LENGTH | USPG_BINARY */
     int32_t coeff_dtype; /* USPG_F32 | USPG_F16 | USPG_BF16 */
-    int32_t reserved0, reserved1;
+    int32_t store_form;  /* USPG_STORE_REPRESENTATIVES | USPG_STORE_SEGMENTS (binary only) */
+    int32_t reserved1;
 } uspg_coeff_opts;
 
 typedef struct {

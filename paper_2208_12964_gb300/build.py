@@ -3,8 +3,8 @@
 ``python -m paper_2208_12964_gb300.build`` compiles each translation unit with
 nvcc in parallel and links ``_lib/libuspg.so``.  The generator is compiled
 with ``-fmad=false`` so its FP64 crossings are formed with separately rounded
-operations; so is the resample, whose pixel-centre classification follows the
-same rule.
+operations; so are the segment store (the same crossings) and the resample,
+whose pixel-centre classification follows the same rule.
 """
 from __future__ import annotations
 
@@ -27,6 +27,7 @@ UNITS = {
     "resample.cu": ["-fmad=false"],
     "batch.cu": [],
     "server.cu": [],
+    "segments.cu": ["-fmad=false"],
 }
 
 

@@ -218,6 +218,7 @@ long long ctx_device_bytes(const uspg_ctx *c)
     long long b = 4LL * c->n_cells + 4LL * c->scan.n_views * c->n_rays + 12LL * c->n_rays;  // image, projections, scratch
     if (c->store_src) return b;
     b += (long long)sizeof(RingEntry) * c->n_rings + 24LL * c->cells_per_slab;  // ring table, boundaries
+    if (c->d_seg_ptr) b += 20LL * c->n_segments + 9LL * (c->n_rays + 1) + 8LL * c->scan.n_views;
     if (c->d_row_ptr) {
         b += 8LL * (rows + 1) * 2 + 4LL * rows + 4LL * (rows + 1);                       // row pointers, counts, max
         b += (long long)c->cap_idx * (4 + wb + 8) + 4LL * c->cap_grp;                    // rows, FP64 weights, groups
@@ -273,8 +274,13 @@ uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, 
     }
     int wm = opts ? opts->weight_mode : USPG_LENGTH;
     int dt = opts ? opts->coeff_dtype : USPG_F32;
+    int sf = opts ? opts->store_form : USPG_STORE_REPRESENTATIVES;
     if (wm != USPG_LENGTH && wm != USPG_BINARY) return fail(nullptr, USPG_EINVAL, "unknown weight_mode");
     if (dt != USPG_F32 && dt != USPG_F16 && dt != USPG_BF16) return fail(nullptr, USPG_EINVAL, "unknown coeff_dtype");
+    if (sf != USPG_STORE_REPRESENTATIVES && sf != USPG_STORE_SEGMENTS)
+        return fail(nullptr, USPG_EINVAL, "unknown store_form");
+    if (sf == USPG_STORE_SEGMENTS && wm != USPG_BINARY)
+        return fail(nullptr, USPG_EINVAL, "the segment store holds binary coefficients (weight_mode USPG_BINARY)");
 
     uspg_ctx *c = new uspg_ctx();
     c->n_rings = g.n_rings;
@@ -291,7 +297,9 @@ uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, 
     c->mir.n_u = s.n_u;
     c->mir.n_v = s.geometry == USPG_CONE_3D ? s.n_v : 1;
     c->mir.n_slabs = ns;
-    c->mir.on = s.geometry == USPG_CONE_3D && s.n_v >= 2 && c->z_min == -0.5 * (double)ns * c->h;
+    c->store_form = sf;
+    c->mir.on = sf == USPG_STORE_REPRESENTATIVES && s.geometry == USPG_CONE_3D && s.n_v >= 2 &&
+                c->z_min == -0.5 * (double)ns * c->h;
     c->mir.n_rows = c->mir.on ? (s.n_v + 1) / 2 * s.n_u : c->n_rays;
     c->weight_mode = wm;
     c->dtype = dt;
@@ -371,6 +379,7 @@ void uspg_destroy(uspg_ctx *c)
     free_state(c);
     if (!c->store_src) {
         free_store(c);
+        free_segments(c);
         cudaFree(c->d_ring);
         cudaFree(c->d_bdir);
         cudaFree(c->d_bdirf);
@@ -407,7 +416,7 @@ uspg_status uspg_build_coeffs(uspg_ctx *c, uspg_stream stream)
     cudaStream_t s = (cudaStream_t)stream;
     c->built = false;
     c->store_moved = false;
-    st = build_store(c, s);
+    st = c->store_form == USPG_STORE_SEGMENTS ? build_segments(c, s) : build_store(c, s);
     if (st) return st;
     if (c->store_moved) {  // captured graphs point at the old buffers
         for (auto &kv : c->graphs) {
@@ -431,6 +440,21 @@ uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
     o->cells_per_slab = c->cells_per_slab;
     o->n_rays = c->n_rays;
     o->n_views = c->scan.n_views;
+    if (c->store_form == USPG_STORE_SEGMENTS) {
+        // one store for every view: 20 bytes a segment, row pointers, turn
+        // directions and view angles; the full binary matrix would hold a
+        // 4-byte cell id per nonzero and a row pointer per (view, ray)
+        o->n_reps = 1;
+        o->nnz_store = c->n_segments;
+        o->nnz_all_views = c->nnz_all_views;
+        o->store_bytes = c->n_segments * 20 + 8LL * (c->n_rays + 1) + c->n_rays + 8LL * c->scan.n_views;
+        o->full_matrix_bytes = 4LL * c->nnz_all_views + 8LL * ((long long)c->scan.n_views * c->n_rays + 1);
+        o->max_row = c->gen.max_row;
+        o->gcd = c->G;
+        o->mirrored = 0;
+        o->slices = 0;
+        return USPG_OK;
+    }
     o->n_reps = c->n_reps;
     o->nnz_store = c->gen.nnz;
     o->nnz_all_views = c->nnz_all_views;
@@ -456,6 +480,18 @@ uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t 
     if (!c || !n) return fail(c, USPG_EINVAL, "NULL argument");
     if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
     if (view < 0 || view >= c->scan.n_views || ray < 0 || ray >= c->n_rays) return fail(c, USPG_EINVAL, "bad view/ray");
+    if (c->store_form == USPG_STORE_SEGMENTS) {
+        std::vector<long long> cl;
+        uspg_status st = segment_row(c, view, ray, cl);
+        if (st) return st;
+        *n = (int32_t)cl.size();
+        if ((long long)cl.size() > cap) return fail(c, USPG_EINVAL, "row longer than cap");
+        for (size_t q = 0; q < cl.size(); q++) {
+            cells[q] = cl[q];
+            w[q] = 1.0;
+        }
+        return USPG_OK;
+    }
     int rep = c->rep_of_view[view];
     bool flip = c->mir.on && ray >= c->mir.n_rows;  // a mirrored row: stored as its mirror ray
     int stored = flip ? mirror_ray(ray, c->mir.n_u, c->mir.n_v) : ray;
@@ -653,9 +689,11 @@ uspg_status uspg_mart(uspg_ctx *c, const uspg_mart_opts *o, uspg_stream stream)
             return fail(c, USPG_EINVAL, "unknown update rule");
         if (o->stop_tol < 0.0) return fail(c, USPG_EINVAL, "stop_tol must be >= 0");
         c->last_sweeps = -1;
-        return launch_sequential(c, o, s);
+        return c->store_form == USPG_STORE_SEGMENTS ? launch_sequential_segments(c, o, s) : launch_sequential(c, o, s);
     }
     if (o->schedule != USPG_PER_VIEW) return fail(c, USPG_EINVAL, "unknown schedule");
+    if (c->store_form == USPG_STORE_SEGMENTS)
+        return fail(c, USPG_EUNSUPPORTED, "the segment store serves the ray-sequential schedule");
     if (o->update_rule != USPG_POWER)
         return fail(c, USPG_EUNSUPPORTED, "the per-view schedule uses the power (geometric-mean) update");
     if (o->stop_tol != 0.0) return fail(c, USPG_EUNSUPPORTED, "stop_tol applies to the sequential schedule");
@@ -669,6 +707,8 @@ uspg_status uspg_mart_kernel_times(uspg_ctx *c, const uspg_mart_opts *o, float *
     if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
     if (!c->have_proj) return fail(c, USPG_ENOTREADY, "projections not set");
     if (o->schedule != USPG_PER_VIEW) return fail(c, USPG_EINVAL, "kernel timing covers the per-view schedule");
+    if (c->store_form == USPG_STORE_SEGMENTS)
+        return fail(c, USPG_EUNSUPPORTED, "the segment store serves the ray-sequential schedule");
     int nv = c->scan.n_views;
     long long steps = (long long)o->iterations * nv;
     if (steps > cap) return fail(c, USPG_EINVAL, "cap < iterations * n_views");
@@ -703,6 +743,8 @@ uspg_status uspg_autotune(uspg_ctx *c, int32_t *choice, uspg_stream stream)
 {
     if (!c) return fail(c, USPG_EINVAL, "NULL context");
     if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    if (c->store_form == USPG_STORE_SEGMENTS)
+        return fail(c, USPG_EUNSUPPORTED, "the per-view kernels read the representative store");
     if (!c->have_proj) return fail(c, USPG_ENOTREADY, "projections not set");
     cudaStream_t s = (cudaStream_t)stream;
     float *saved = nullptr;
@@ -793,6 +835,8 @@ uspg_status uspg_forward_project(uspg_ctx *c, int32_t view, float *out, uspg_str
     if (!c || !out) return fail(c, USPG_EINVAL, "NULL argument");
     if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
     if (view < 0 || view >= c->scan.n_views) return fail(c, USPG_EINVAL, "bad view");
+    if (c->store_form == USPG_STORE_SEGMENTS)
+        return fail(c, USPG_EUNSUPPORTED, "the per-view kernels read the representative store");
     return launch_forward_view(c, view, out, nullptr, (cudaStream_t)stream);
 }
 

@@ -195,6 +195,10 @@ uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_
             uspg_batch_destroy(b);
             return fail(nullptr, USPG_ENOTREADY, "batch: every context needs coefficients and projections");
         }
+        if (c->store_form == USPG_STORE_SEGMENTS) {
+            uspg_batch_destroy(b);
+            return fail(nullptr, USPG_EUNSUPPORTED, "batch: the per-view kernels read the representative store");
+        }
         if (c->dtype != b->dtype) {
             uspg_batch_destroy(b);
             return fail(nullptr, USPG_EINVAL, "batch: all contexts must store coefficients in one dtype");

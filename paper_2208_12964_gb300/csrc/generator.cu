@@ -516,8 +516,7 @@ __global__ void k_group_rays(const long long *row_ptr, long long n_all, int n_ro
 
 static unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-template <typename WT>
-static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
+Geometry make_geometry(const uspg_ctx *c)
 {
     Geometry g{};
     g.geometry = c->scan.geometry;
@@ -539,6 +538,18 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     g.d_sd = c->scan.src_to_det;
     g.cells_per_slab = c->cells_per_slab;
     g.n_rows = c->mir.n_rows;
+    return g;
+}
+
+cudaError_t scan_counts(const int *in, long long n, long long *out, cudaStream_t s)
+{
+    return exclusive_scan<int>(in, n, 1, out, s);
+}
+
+template <typename WT>
+static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
+{
+    Geometry g = make_geometry(c);
     const Mirror M = c->mir;
     const int n_rows = M.n_rows;
 

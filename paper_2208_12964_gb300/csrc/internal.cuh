@@ -199,12 +199,30 @@ struct uspg_ctx {
     // set on a context that reads another context's store and tables (which
     // must outlive it); its image, projections, scratch and graphs are its own
     const uspg_ctx *store_src = nullptr;
+    // USPG_STORE_SEGMENTS: the first view's segments (binary model, Algorithm 1)
+    int store_form = USPG_STORE_REPRESENTATIVES;
+    long long *d_seg_ptr = nullptr;   // [n_rays + 1] first segment of each ray
+    uint64_t *d_seg_fa = nullptr;     // [segments] azimuth where the segment starts (fixed turns)
+    uint64_t *d_seg_fb = nullptr;     // [segments] azimuth where it ends
+    uint32_t *d_seg_rs = nullptr;     // [segments] slab << 22 | ring << 12 | back (see segments.cu)
+    signed char *d_seg_dir = nullptr; // [n_rays] direction the azimuth turns along the ray (+1, -1, 0)
+    uint64_t *d_view_turns = nullptr; // [n_views] source angle of each view (fixed turns)
+    long long n_segments = 0;
+    int max_segments = 0;             // longest ray, in segments
 };
 
 namespace uspg {
 
 // generator.cu
 uspg_status build_store(uspg_ctx *c, cudaStream_t s);
+Geometry make_geometry(const uspg_ctx *c);
+// exclusive prefix sum of n counts into out[0..n] (out[n] = total)
+cudaError_t scan_counts(const int *in, long long n, long long *out, cudaStream_t s);
+// segments.cu: the first view's segment store of the binary model
+uspg_status build_segments(uspg_ctx *c, cudaStream_t s);
+uspg_status launch_sequential_segments(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s);
+uspg_status segment_row(uspg_ctx *c, int view, int ray, std::vector<long long> &cells);
+void free_segments(uspg_ctx *c);
 // mart.cu
 uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s);
 uspg_status launch_backward_view(uspg_ctx *c, int view, float lambda, cudaStream_t s);

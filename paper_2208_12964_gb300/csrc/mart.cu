@@ -528,6 +528,8 @@ extern "C" uspg_status uspg_forward_project_noalloc(const uspg_ctx *cc, int32_t 
                         std::to_string(USPG_NOALLOC_MAX_RAYS) + "-ray accumulator");
     if (view < 0 || view >= c->scan.n_views) return fail(c, USPG_EINVAL, "bad view");
     if (!c->built) return fail(c, USPG_ENOTREADY, "coefficients not built");
+    if (c->store_form == USPG_STORE_SEGMENTS)
+        return fail(c, USPG_EUNSUPPORTED, "the per-view kernels read the representative store");
     float *acc = nullptr;
     USPG_CUDA(c, noalloc_acc(&acc));
     cudaStream_t s = (cudaStream_t)stream;

@@ -479,6 +479,8 @@ uspg_status uspg_server_submit(uspg_server *s, const uspg_job *job, uint64_t *id
         return uspg::fail(nullptr, USPG_EINVAL, "server: unknown schedule");
     if (m.schedule == USPG_PER_VIEW && m.update_rule != USPG_POWER)
         return uspg::fail(nullptr, USPG_EUNSUPPORTED, "server: per-view jobs use the power update");
+    if (job->coeff.store_form != USPG_STORE_REPRESENTATIVES)
+        return uspg::fail(nullptr, USPG_EUNSUPPORTED, "server: jobs use the representative store");
     int ns = job->scan.geometry == USPG_CONE_3D ? job->scan.n_v : 1;
     long long n = (long long)job->scan.n_views * job->scan.n_u * ns;
     if (job->scan.n_views < 1 || job->scan.n_u < 1 || ns < 1 || n <= 0)

@@ -28,6 +28,8 @@ import numpy as np
 SECT_6N, SECT_4_2N1, SECT_CUSTOM = 0, 1, 2
 PARALLEL_2D, CONE_3D, FAN_2D = 0, 1, 2
 POWER, LINEAR_EQ18 = 0, 1
+LENGTH, BINARY = 0, 1
+STORE_REPRESENTATIVES, STORE_SEGMENTS = 0, 1
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -74,6 +76,8 @@ def workload(name: str) -> dict:
                     d_so=1.0, d_sd=2.0, iterations=10, lam=0.2, schedule="sequential", seed=1, noise=False)
     if name == "2d-fan-128r-50v-101":
         return fan_workload(128, 50, name=name)
+    if name == "2d-fan-128r-50v-101-segments":  # the paper's binary coefficients from the first view's segments
+        return dict(fan_workload(128, 50, name=name), weight_mode=BINARY, store_form=STORE_SEGMENTS)
     if name == "3d-cone-128r-128s-90v-256":
         return cone_workload(128, 128, 90, 256, iterations=5, lam=0.1, seed=2, name=name)
     if name == "3d-cone-256r-256s-180v-512":

@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EBUSY, ENOTREADY, EDEVICE = r
 SECT_6N, SECT_4_2N1, SECT_CUSTOM = 0, 1, 2
 PARALLEL_2D, CONE_3D, FAN_2D = 0, 1, 2
 LENGTH, BINARY = 0, 1
+STORE_REPRESENTATIVES, STORE_SEGMENTS = 0, 1
 F32, F16, BF16 = 0, 1, 2
 SEQUENTIAL, PER_VIEW = 0, 1
 POWER, LINEAR_EQ18 = 0, 1
@@ -45,7 +46,7 @@ class ScanDesc(C.Structure):
 
 
 class CoeffOpts(C.Structure):
-    _fields_ = [("weight_mode", C.c_int32), ("coeff_dtype", C.c_int32), ("reserved0", C.c_int32),
+    _fields_ = [("weight_mode", C.c_int32), ("coeff_dtype", C.c_int32), ("store_form", C.c_int32),
                 ("reserved1", C.c_int32)]
 
 
@@ -156,7 +157,7 @@ def _ptr(x):
     return int(x.data_ptr())
 
 
-def descs_from_spec(spec: dict, dtype: int = F32, weight_mode: int = LENGTH):
+def descs_from_spec(spec: dict, dtype: int = F32, weight_mode: int | None = None, store_form: int | None = None):
     """C descriptors for a workload description (see synth.workload)."""
     g = GridDesc(n_rings=spec["n_rings"], sector_rule=spec["sector_rule"], sectors=None, ring_width=spec["r"],
                  n_slabs=spec["n_slabs"] if spec["geometry"] == CONE_3D else 1, reserved=0,
@@ -168,7 +169,11 @@ def descs_from_spec(spec: dict, dtype: int = F32, weight_mode: int = LENGTH):
     s = ScanDesc(geometry=spec["geometry"], n_views=spec["n_views"], arc_num=spec["arc_num"],
                  arc_den=spec["arc_den"], n_u=spec["n_u"], n_v=spec["n_v"] if spec["geometry"] == CONE_3D else 1,
                  du=spec["du"], dv=spec["dv"], src_to_axis=spec["d_so"], src_to_det=spec["d_sd"])
-    o = CoeffOpts(weight_mode=weight_mode, coeff_dtype=dtype)
+    if weight_mode is None:
+        weight_mode = spec.get("weight_mode", LENGTH)
+    if store_form is None:
+        store_form = spec.get("store_form", STORE_REPRESENTATIVES)
+    o = CoeffOpts(weight_mode=weight_mode, coeff_dtype=dtype, store_form=store_form)
     return g, s, o, keep
 
 

@@ -8,9 +8,10 @@ from paper_2208_12964_gb300 import synth
 ORACLE_KEYS = dict(oracle.Problem._fields_)
 
 
-def oracle_for(spec, threads=8, weight_mode=oracle.LENGTH):
+def oracle_for(spec, threads=8, weight_mode=None, store_form=None):
     d = {k: v for k, v in spec.items() if k in ORACLE_KEYS}
-    d["weight_mode"] = weight_mode
+    d["weight_mode"] = spec.get("weight_mode", oracle.LENGTH) if weight_mode is None else weight_mode
+    d["store_form"] = spec.get("store_form", oracle.STORE_ROWS) if store_form is None else store_form
     if spec.get("custom_sectors") is not None:
         d["custom_sectors"] = spec["custom_sectors"]
     return oracle.Oracle(d, threads=threads)
@@ -19,13 +20,12 @@ def oracle_for(spec, threads=8, weight_mode=oracle.LENGTH):
 class Gpu:
     """One libuspg context for a workload description."""
 
-    def __init__(self, spec, dtype=None, weight_mode=None):
+    def __init__(self, spec, dtype=None, weight_mode=None, store_form=None):
         from paper_2208_12964_gb300 import uspg
 
         self.U = uspg
         dtype = uspg.F32 if dtype is None else dtype
-        weight_mode = uspg.LENGTH if weight_mode is None else weight_mode
-        g, s, o, self._keep = uspg.descs_from_spec(spec, dtype, weight_mode)
+        g, s, o, self._keep = uspg.descs_from_spec(spec, dtype, weight_mode, store_form)
         self.ctx = uspg.uspg_create(g, s, o)
         self.spec = spec
 
