@@ -17,8 +17,8 @@
 // same separately rounded operations as their definitions so the index lists
 // do not depend on contraction.
 //
-// Passes: size (FP32 bound) -> scan -> fill (FP64 weights) -> convert to the
-// stored dtype -> cell-major store (count per cell, slice widths, scan,
+// Passes: size (FP32 bound) -> scan -> fill (FP64 walk, then the row in the
+// stored dtype) -> cell-major store (count per cell, slice widths, scan,
 // scatter, per-cell sort by ray key so the layout is deterministic, lanes
 // ordered by count).  Centred cone scans trace and store only the lower
 // detector rows (z-mirror); the cell-major store then holds the lower and
@@ -80,13 +80,52 @@ __global__ void __launch_bounds__(128) k_count(Geometry g, const RingEntry *rt, 
     counts[row] = sink.n;
 }
 
+// ---- stored precision -----------------------------------------------------
+
+template <typename WT>
+__device__ __forceinline__ WT to_w(float x);
+template <>
+__device__ __forceinline__ float to_w<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __half to_w<__half>(float x)
+{
+    __half h = __float2half_rn(x);
+    if (x > 0.0f && __half2float(h) == 0.0f) h = __ushort_as_half((unsigned short)1);  // keep w > 0
+    return h;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_w<__nv_bfloat16>(float x)
+{
+    return __float2bfloat16_rn(x);
+}
+__device__ __forceinline__ float w_to_f(float x) { return x; }
+__device__ __forceinline__ float w_to_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ float w_to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// A row in the stored precision (FP64 length / scale, or 1 when binary;
+// padding slots 0); returns its largest stored weight.
+template <typename WT>
+__device__ float store_row(const double *w64, long long b, long long e, int n, int binary, double inv_scale, WT *w)
+{
+    float mx = 0.0f;
+    for (long long q = b; q < e; q++) {
+        WT v = q - b < n ? to_w<WT>((float)(binary ? 1.0 : w64[q] * inv_scale)) : to_w<WT>(0.0f);
+        w[q] = v;
+        float fv = w_to_f(v);
+        mx = fv > mx ? fv : mx;
+    }
+    return mx;
+}
+
 // FP64 walk into the row's slots [row_ptr[i], row_ptr[i+1]); writes the
-// entry count to counts[i] and pads the rest of the row (cell 0, weight 0).
-// A row with more entries than slots raises kStatusCountMismatch.
+// entry count to counts[i], pads the rest of the row (cell 0, weight 0), and
+// stores the row in the stored precision with its largest weight.  A row
+// with more entries than slots raises kStatusCountMismatch.
 template <int MAXR>
 __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, const double2 *bdir,
                                               const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                                              const long long *row_ptr, uint32_t *idx, double *w64, int *status)
+                                              const long long *row_ptr, uint32_t *idx, double *w64, int *status,
+                                              int dtype, double inv_scale, void *w, float *rowmax)
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_reps * g.n_rows) return;
@@ -113,25 +152,40 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
         idx[q] = 0;
         w64[q] = 0.0;
     }
+    int binary = g.weight_mode == USPG_BINARY;
+    float mx;
+    if (dtype == USPG_F16) mx = store_row(w64, b, e, sink.n, binary, inv_scale, (__half *)w);
+    else if (dtype == USPG_BF16) mx = store_row(w64, b, e, sink.n, binary, inv_scale, (__nv_bfloat16 *)w);
+    else mx = store_row(w64, b, e, sink.n, binary, inv_scale, (float *)w);
+    rowmax[row] = mx;
 }
+
+// what k_fill writes besides the FP64 rows: stored weights and row maxima
+struct FillOut {
+    int dtype;
+    double inv_scale;
+    void *w;
+    float *rowmax;
+};
 
 template <int MAXR>
 static void launch_walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
                         const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                        const long long *row_ptr, uint32_t *idx, double *w64, int *status)
+                        const long long *row_ptr, uint32_t *idx, double *w64, int *status, const FillOut &fo)
 {
     if (fill)
-        k_fill<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status);
+        k_fill<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status,
+                                          fo.dtype, fo.inv_scale, fo.w, fo.rowmax);
     else
         k_count<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, status);
 }
 
 static void walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
                  const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                 const long long *row_ptr, uint32_t *idx, double *w64, int *status)
+                 const long long *row_ptr, uint32_t *idx, double *w64, int *status, const FillOut &fo = FillOut{})
 {
 #define USPG_WALK(M) \
-    launch_walk<M>(fill, grid, s, g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status)
+    launch_walk<M>(fill, grid, s, g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status, fo)
     if (g.n_rings <= 64) USPG_WALK(64);
     else if (g.n_rings <= 128) USPG_WALK(128);
     else if (g.n_rings <= 256) USPG_WALK(256);
@@ -197,52 +251,6 @@ static cudaError_t exclusive_scan(const T *in, long long n, int pad, long long *
     cudaFreeAsync(sums, s);
     cudaFreeAsync(offs, s);
     return cudaGetLastError();
-}
-
-// ---- stored precision -----------------------------------------------------
-
-template <typename WT>
-__device__ __forceinline__ WT to_w(float x);
-template <>
-__device__ __forceinline__ float to_w<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ __half to_w<__half>(float x)
-{
-    __half h = __float2half_rn(x);
-    if (x > 0.0f && __half2float(h) == 0.0f) h = __ushort_as_half((unsigned short)1);  // keep w > 0
-    return h;
-}
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_w<__nv_bfloat16>(float x)
-{
-    return __float2bfloat16_rn(x);
-}
-__device__ __forceinline__ float w_to_f(float x) { return x; }
-__device__ __forceinline__ float w_to_f(__half x) { return __half2float(x); }
-__device__ __forceinline__ float w_to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
-
-template <typename WT>
-__global__ void k_convert(long long n_rows, const long long *row_ptr, const int *counts, const double *w64, int binary,
-                         double inv_scale, WT *w, float *rowmax)
-{
-    long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= n_rows) return;
-    long long b = row_ptr[row], e = row_ptr[row + 1];
-    long long n = counts[row];
-    float mx = 0.0f;
-    for (long long q = b; q < e; q++) {
-        WT v;
-        if (q - b < n) {
-            double x = binary ? 1.0 : w64[q] * inv_scale;
-            v = to_w<WT>((float)x);
-        } else {
-            v = to_w<WT>(0.0f);
-        }
-        w[q] = v;
-        float fv = w_to_f(v);
-        mx = fv > mx ? fv : mx;
-    }
-    rowmax[row] = mx;
 }
 
 // ---- cell-major store -------------------------------------------------------
@@ -357,9 +365,8 @@ __global__ void k_cell_scatter(const long long *row_ptr, const int *counts, cons
     }
 }
 
-// one thread per (slice, lane): sort the cell's entries by ray id (insertion
-// sort for short columns, heapsort beyond, so a cell crossed by very many rays
-// costs O(n log n)), pad the rest
+// heap step of the in-place column sort (the column's t-th entry is at
+// base + 32 t)
 template <typename WT>
 __device__ void sift_down(uint32_t *ray, WT *w, long long base, int root, int n)
 {
@@ -380,52 +387,6 @@ __device__ void sift_down(uint32_t *ray, WT *w, long long base, int root, int n)
         w[pr] = w[pc];
         w[pc] = tw;
         root = child;
-    }
-}
-
-template <typename WT>
-__global__ void k_cell_finish(long long n_slices, const long long *slice_off, const int *width, const uint32_t *meta,
-                              const RingEntry *rt, long long cps, const int *cell_cnt, uint32_t *sray, WT *sw)
-{
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long sl = t >> 5;
-    int lane = (int)(t & 31);
-    if (sl >= n_slices) return;
-    uint32_t m = meta[sl];
-    int ring = cell_ring(m), sec = cell_sector(m) + lane;
-    int n = 0;
-    if (sec < rt[ring].ng) n = cell_cnt[(long long)cell_slab(m) * cps + rt[ring].head + sec];
-    long long base = slice_off[sl] + lane;
-    int W = width[sl];
-    if (n <= 32) {
-        for (int q = 1; q < n; q++) {
-            uint32_t rv = sray[base + (long long)q * kSlice];
-            WT wv = sw[base + (long long)q * kSlice];
-            int p = q - 1;
-            while (p >= 0 && sray[base + (long long)p * kSlice] > rv) {
-                sray[base + (long long)(p + 1) * kSlice] = sray[base + (long long)p * kSlice];
-                sw[base + (long long)(p + 1) * kSlice] = sw[base + (long long)p * kSlice];
-                p--;
-            }
-            sray[base + (long long)(p + 1) * kSlice] = rv;
-            sw[base + (long long)(p + 1) * kSlice] = wv;
-        }
-    } else {
-        for (int r = n / 2 - 1; r >= 0; r--) sift_down(sray, sw, base, r, n);
-        for (int end = n - 1; end > 0; end--) {
-            long long pe = base + (long long)end * kSlice;
-            uint32_t tr = sray[base];
-            sray[base] = sray[pe];
-            sray[pe] = tr;
-            WT tw = sw[base];
-            sw[base] = sw[pe];
-            sw[pe] = tw;
-            sift_down(sray, sw, base, 0, end);
-        }
-    }
-    for (int q = n; q < W; q++) {
-        sray[base + (long long)q * kSlice] = 0;
-        sw[base + (long long)q * kSlice] = to_w<WT>(0.0f);
     }
 }
 
@@ -462,10 +423,17 @@ __global__ void k_row_stats(const int *counts, long long n_all, int n_rows, Mirr
     if ((threadIdx.x & 31) == 0) atomicMax(&st[2 * n_reps], (unsigned long long)mx);
 }
 
-__global__ void k_set_off(long long *dst, const long long *rel, long long n, long long base)
+// Slice offsets of representative rep: its relative offsets (in slices of
+// 32 slots) after the slots of the earlier representatives, whose slice
+// totals are rep_tot[0 .. rep-1]; records its own total in rep_tot[rep].
+__global__ void k_set_off(long long *dst, const long long *rel, long long n, long long *rep_tot, int rep)
 {
+    long long base = 0;
+    for (int q = 0; q < rep; q++) base += rep_tot[q];
+    base *= kSlice;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = base + rel[i] * kSlice;
+    if (i == 0) rep_tot[rep] = rel[n];
 }
 
 // ---- cell-major store with lanes ordered by ray count ----------------------------
@@ -477,10 +445,32 @@ __global__ void k_set_off(long long *dst, const long long *rel, long long n, lon
 // loaded data, with the absent slots never fetched.  lane_desc[32 s + l] =
 // (source lane << 11) | count.
 
+// Sort and lane order in one pass: one warp per slice, each lane owning one
+// cell whose column sits in arrival order at slice_off + 32 t + lane.  The
+// lane's rank (counts falling from lane 0, ties by lane) and count go to
+// lane_desc; the column, sorted by ray key (a total order: a ray meets a cell
+// once per view, its mirror carries bit 31), goes to slots 32 t + rank of the
+// lane-ordered store.  Columns of up to kOrderRegs entries are sorted in
+// registers by odd-even transposition; longer ones in place first.
+constexpr int kOrderRegs = 8;
+
 template <typename WT>
-__global__ void k_sort_lanes(long long n_slices, const uint32_t *meta, const int *width, const long long *slice_off,
-                             const RingEntry *rt, long long cps, const int *cell_cnt, const uint32_t *sray,
-                             const WT *sw, uint16_t *lane_desc, uint32_t *dray, WT *dw)
+__device__ __forceinline__ void cx(uint32_t &ra, WT &wa, uint32_t &rb, WT &wb)
+{
+    if (ra > rb) {
+        uint32_t t = ra;
+        ra = rb;
+        rb = t;
+        WT u = wa;
+        wa = wb;
+        wb = u;
+    }
+}
+
+template <typename WT>
+__global__ void k_cell_order(long long n_slices, const uint32_t *meta, const long long *slice_off,
+                             const RingEntry *rt, long long cps, const int *cell_cnt, uint32_t *sray, WT *sw,
+                             uint16_t *lane_desc, uint32_t *dray, WT *dw)
 {
     long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -488,19 +478,64 @@ __global__ void k_sort_lanes(long long n_slices, const uint32_t *meta, const int
     uint32_t m = meta[sl];
     int ring = cell_ring(m), sec = cell_sector(m) + lane;
     int cnt = sec < rt[ring].ng ? cell_cnt[(long long)cell_slab(m) * cps + rt[ring].head + sec] : 0;
-    int rank = 0;  // position of this lane in descending count order (ties by lane)
+    int rank = 0;
     for (int o = 0; o < 32; o++) {
         int co = __shfl_sync(0xffffffffu, cnt, o);
         rank += (co > cnt) || (co == cnt && o < lane);
     }
     lane_desc[sl * 32 + rank] = (uint16_t)((lane << 11) | cnt);
-    long long off = slice_off[sl];
-    int W = width[sl];
-    for (int t = 0; t < W; t++) {
-        if (t < cnt) {
-            dray[off + (long long)t * kSlice + rank] = sray[off + (long long)t * kSlice + lane];
-            dw[off + (long long)t * kSlice + rank] = sw[off + (long long)t * kSlice + lane];
+    long long off = slice_off[sl], base = off + lane;
+    if (cnt <= kOrderRegs) {
+        uint32_t r[kOrderRegs];
+        WT w[kOrderRegs];
+#pragma unroll
+        for (int t = 0; t < kOrderRegs; t++) {
+            r[t] = t < cnt ? sray[base + (long long)t * kSlice] : 0xffffffffu;  // absent entries sort last
+            w[t] = t < cnt ? sw[base + (long long)t * kSlice] : to_w<WT>(0.0f);
         }
+#pragma unroll
+        for (int pass = 0; pass < kOrderRegs; pass++) {
+#pragma unroll
+            for (int t = pass & 1; t + 1 < kOrderRegs; t += 2) cx(r[t], w[t], r[t + 1], w[t + 1]);
+        }
+#pragma unroll
+        for (int t = 0; t < kOrderRegs; t++) {
+            if (t < cnt) {
+                dray[off + (long long)t * kSlice + rank] = r[t];
+                dw[off + (long long)t * kSlice + rank] = w[t];
+            }
+        }
+        return;
+    }
+    if (cnt <= 32) {  // insertion sort in place
+        for (int q = 1; q < cnt; q++) {
+            uint32_t rv = sray[base + (long long)q * kSlice];
+            WT wv = sw[base + (long long)q * kSlice];
+            int p = q - 1;
+            while (p >= 0 && sray[base + (long long)p * kSlice] > rv) {
+                sray[base + (long long)(p + 1) * kSlice] = sray[base + (long long)p * kSlice];
+                sw[base + (long long)(p + 1) * kSlice] = sw[base + (long long)p * kSlice];
+                p--;
+            }
+            sray[base + (long long)(p + 1) * kSlice] = rv;
+            sw[base + (long long)(p + 1) * kSlice] = wv;
+        }
+    } else {  // heapsort: a cell crossed by very many rays costs O(n log n)
+        for (int q = cnt / 2 - 1; q >= 0; q--) sift_down(sray, sw, base, q, cnt);
+        for (int e = cnt - 1; e > 0; e--) {
+            long long pe = base + (long long)e * kSlice;
+            uint32_t tr = sray[base];
+            sray[base] = sray[pe];
+            sray[pe] = tr;
+            WT tw = sw[base];
+            sw[base] = sw[pe];
+            sw[pe] = tw;
+            sift_down(sray, sw, base, 0, e);
+        }
+    }
+    for (int t = 0; t < cnt; t++) {
+        dray[off + (long long)t * kSlice + rank] = sray[base + (long long)t * kSlice];
+        dw[off + (long long)t * kSlice + rank] = sw[base + (long long)t * kSlice];
     }
 }
 
@@ -604,8 +639,9 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
             c->cap_idx = need;
             c->store_moved = true;
         }
+        FillOut fo{c->dtype, 1.0 / c->w_scale, c->d_w, c->d_rowmax};
         walk(true, nblk(nrows, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, nreps, d_counts,
-             c->d_row_ptr, c->d_idx, c->d_w64, c->d_status);
+             c->d_row_ptr, c->d_idx, c->d_w64, c->d_status, fo);
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
         int st = 0;
@@ -616,12 +652,6 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
         c->gen_fallbacks++;
     }
-    double *d_w64 = c->d_w64;
-    k_convert<WT><<<nblk(nrows, 256), 256, 0, s>>>(nrows, c->d_row_ptr, d_counts, d_w64,
-                                                   c->weight_mode == USPG_BINARY, 1.0 / c->w_scale, (WT *)c->d_w,
-                                                   c->d_rowmax);
-    launch_counter()++;
-    USPG_CUDA(c, cudaGetLastError());
 
     // statistics on the device: per-representative nonzeros and longest row
     USPG_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(long long) * (2 * nreps + 1), s));
@@ -648,11 +678,11 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     // cell-major store, one representative at a time
     int *d_cell_cnt = c->d_cell_cnt, *d_cell_fill = c->d_cell_fill;
     long long *d_rel = c->d_rel;
-    // pass 1: slice widths and offsets
-    long long sell = 0;
-    c->h_sell_base.assign(nreps + 1, 0);
+    // pass 1: slice widths and offsets (every representative's slots follow
+    // the earlier ones'; the totals are read back once)
+    long long *d_rep_tot = nullptr;
+    USPG_CUDA(c, cudaMallocAsync(&d_rep_tot, sizeof(long long) * (nreps + 1), s));
     for (int rep = 0; rep < nreps; rep++) {
-        c->h_sell_base[rep] = sell;
         const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
         const int *cn = d_counts + (long long)rep * n_rows;
         USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
@@ -665,13 +695,21 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                                                                c->cells_per_slab, d_cell_cnt, wd, md, c->d_status);
         launch_counter()++;
         USPG_CUDA(c, exclusive_scan<int>(wd, n_slices, 1, d_rel, s));
-        k_set_off<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_off + rep * n_slices, d_rel, n_slices, sell);
+        k_set_off<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_off + rep * n_slices, d_rel, n_slices, d_rep_tot,
+                                                      rep);
         launch_counter()++;
-        long long tot = 0;
-        USPG_CUDA(c, cudaMemcpyAsync(&tot, d_rel + n_slices, sizeof(long long), cudaMemcpyDeviceToHost, s));
-        USPG_CUDA(c, cudaStreamSynchronize(s));
-        sell += tot * kSlice;
-        if (tot * kSlice >= (1LL << 32)) return fail(c, USPG_EUNSUPPORTED, "a view's cell-major store exceeds 2^32 slots");
+    }
+    std::vector<long long> rep_tot(nreps);
+    USPG_CUDA(c, cudaMemcpyAsync(rep_tot.data(), d_rep_tot, sizeof(long long) * nreps, cudaMemcpyDeviceToHost, s));
+    USPG_CUDA(c, cudaFreeAsync(d_rep_tot, s));
+    USPG_CUDA(c, cudaStreamSynchronize(s));
+    long long sell = 0;
+    c->h_sell_base.assign(nreps + 1, 0);
+    for (int rep = 0; rep < nreps; rep++) {
+        c->h_sell_base[rep] = sell;
+        if (rep_tot[rep] * kSlice >= (1LL << 32))
+            return fail(c, USPG_EUNSUPPORTED, "a view's cell-major store exceeds 2^32 slots");
+        sell += rep_tot[rep] * kSlice;
     }
     c->h_sell_base[nreps] = sell;
     {
@@ -724,15 +762,9 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
             rp, cn, c->d_idx, (const WT *)c->d_w, n_rows, M, c->d_ring, c->cells_per_slab, c->slices_per_slab, so,
             d_cell_fill, c->d_sray, (WT *)c->d_sw);
         launch_counter()++;
-        k_cell_finish<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(n_slices, so, c->d_slice_width + rep * n_slices,
-                                                                   c->d_slice_meta + rep * n_slices, c->d_ring,
-                                                                   c->cells_per_slab, d_cell_cnt, c->d_sray,
-                                                                   (WT *)c->d_sw);
-        launch_counter()++;
-        k_sort_lanes<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(
-            n_slices, c->d_slice_meta + rep * n_slices, c->d_slice_width + rep * n_slices, so, c->d_ring,
-            c->cells_per_slab, d_cell_cnt, c->d_sray, (const WT *)c->d_sw, c->d_lane_desc + 32 * rep * n_slices,
-            c->d_cm_ray, (WT *)c->d_cm_w);
+        k_cell_order<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(
+            n_slices, c->d_slice_meta + rep * n_slices, so, c->d_ring, c->cells_per_slab, d_cell_cnt, c->d_sray,
+            (WT *)c->d_sw, c->d_lane_desc + 32 * rep * n_slices, c->d_cm_ray, (WT *)c->d_cm_w);
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
     }
