@@ -748,22 +748,20 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_lane_desc, sizeof(uint16_t) * 32 * n_slices * nreps));
         c->store_moved = true;
     }
-    // pass 2: scatter each row entry to its cell's column, then sort and pad
+    // pass 2: scatter each row entry to its cell's column, then sort it into the
+    // lane-ordered store
     for (int rep = 0; rep < nreps; rep++) {
         const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
         const int *cn = d_counts + (long long)rep * n_rows;
         const long long *so = c->d_slice_off + rep * n_slices;
-        USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
         USPG_CUDA(c, cudaMemsetAsync(d_cell_fill, 0, sizeof(int) * c->n_cells, s));
-        k_cell_count<<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, n_rows, M, c->d_ring,
-                                                                       c->cells_per_slab, d_cell_cnt);
-        launch_counter()++;
         k_cell_scatter<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(
             rp, cn, c->d_idx, (const WT *)c->d_w, n_rows, M, c->d_ring, c->cells_per_slab, c->slices_per_slab, so,
             d_cell_fill, c->d_sray, (WT *)c->d_sw);
         launch_counter()++;
+        // the scatter's slot counters now hold every cell's count
         k_cell_order<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(
-            n_slices, c->d_slice_meta + rep * n_slices, so, c->d_ring, c->cells_per_slab, d_cell_cnt, c->d_sray,
+            n_slices, c->d_slice_meta + rep * n_slices, so, c->d_ring, c->cells_per_slab, d_cell_fill, c->d_sray,
             (WT *)c->d_sw, c->d_lane_desc + 32 * rep * n_slices, c->d_cm_ray, (WT *)c->d_cm_w);
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());

@@ -5,6 +5,8 @@
 
 #include "internal.cuh"
 
+#include <cstring>
+
 #ifdef __CUDACC__
 #define USPG_HD __host__ __device__
 #else
@@ -12,6 +14,23 @@
 #endif
 
 namespace uspg {
+
+// a < b for finite FP64 values of which at least one is non-negative (the
+// line parameters the walk compares: segment ends and accepted crossings lie
+// in [0, 1], candidates may be negative, the sentinel is 2): the order of
+// the IEEE bit patterns as signed integers, an integer compare instead of an
+// FP64 one (GB300's FP64 pipe is the walk's bottleneck).
+USPG_HD inline bool lt(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(a) < __double_as_longlong(b);
+#else
+    long long x, y;
+    memcpy(&x, &a, sizeof x);
+    memcpy(&y, &b, sizeof y);
+    return x < y;
+#endif
+}
 
 USPG_HD inline void flag(int *status, int bit)
 {
@@ -226,7 +245,7 @@ template <class Sink>
 USPG_HD inline void piece(const Geometry &g, const RingEntry *rt, const Ray &R, double la, double lb, Sink &sink)
 {
     double len = (lb - la) * R.L;
-    if (!(len >= R.min_len)) return;
+    if (lt(len, R.min_len)) return;
     uint32_t cell;
     if (!classify_fast(g, rt, R, la, lb, &cell)) cell = classify_exact(g, rt, R, la, lb);
     sink.emit(cell, len);
@@ -353,7 +372,7 @@ struct RStream {
             if (den == 0.0) continue;
             double num = R.S[0] * sj - R.S[1] * cj;
             double l = -num / den;
-            if (!(l > sa && l < sb)) continue;
+            if (!(lt(sa, l) && lt(l, sb))) continue;
             bool inside = rhof >= (float)rin + tolr && rhof <= (float)rout - tolr;
             if (!inside) {  // near a vertex: the exact test decides
                 double px = R.S[0] + l * R.dx, py = R.S[1] + l * R.dy;
@@ -374,7 +393,7 @@ USPG_HD void walk_segment(const Geometry &g, const RingEntry *rt, const double2 
                              double sa, double sb, ZStream &zs, Sink &sink, int *status)
 {
     if (!(sb > sa)) return;
-    while (zs.next <= sa) zs.advance(g, R);  // planes of earlier segments, or on their common end
+    while (!lt(sa, zs.next)) zs.advance(g, R);  // planes of earlier segments, or on their common end
     double prev = sa;
     if (ring == 0) {
         // all sectors of ring 0 meet on the axis: test every boundary and the
@@ -413,13 +432,14 @@ USPG_HD void walk_segment(const Geometry &g, const RingEntry *rt, const double2 
         int q = 0;
         for (;;) {
             double rn = q < nx ? xs[q] : 2.0;
-            double nxt = rn < zs.next ? rn : zs.next;
-            if (!(nxt < sb)) break;
-            if (nxt > prev) {
+            bool take_r = !lt(zs.next, rn);
+            double nxt = take_r ? rn : zs.next;
+            if (!lt(nxt, sb)) break;
+            if (lt(prev, nxt)) {
                 piece(g, rt, R, prev, nxt, sink);
                 prev = nxt;
             }
-            if (rn <= zs.next) q++;
+            if (take_r) q++;
             else zs.advance(g, R);
         }
     } else {
@@ -427,17 +447,18 @@ USPG_HD void walk_segment(const Geometry &g, const RingEntry *rt, const double2 
         rs.init(g, rt, R, ring, sa, sb);
         rs.advance(R, bdir, bdirf, sa, sb);
         for (;;) {
-            double nxt = rs.next < zs.next ? rs.next : zs.next;
-            if (!(nxt < sb)) break;
-            if (nxt > prev) {
+            bool take_r = !lt(zs.next, rs.next);  // rs.next <= zs.next
+            double nxt = take_r ? rs.next : zs.next;
+            if (!lt(nxt, sb)) break;
+            if (lt(prev, nxt)) {
                 piece(g, rt, R, prev, nxt, sink);
                 prev = nxt;
             }
-            if (rs.next <= zs.next) rs.advance(R, bdir, bdirf, sa, sb);
+            if (take_r) rs.advance(R, bdir, bdirf, sa, sb);
             else zs.advance(g, R);
         }
     }
-    if (sb > prev) piece(g, rt, R, prev, sb, sink);
+    if (lt(prev, sb)) piece(g, rt, R, prev, sb, sink);
 }
 
 USPG_HD inline double root_k(double m, double r, double d, double a)
