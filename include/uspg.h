@@ -154,8 +154,9 @@ typedef struct {
 /* Validates the description, builds the grid tables (Eq. 1-2) and the view
  * classes (views that share stored rows, Sec. III.C), and allocates nothing
  * on the device yet.  *out receives a new context or NULL.  EINVAL on a
- * non-positive size, sectors < 1, limits exceeded, or a cone detector that
- * misses the cylinder. */
+ * non-positive size, sectors < 1, limits exceeded, a cone or fan source not
+ * outside the grid, a detector that misses it, or the segment store asked
+ * for length weights. */
 uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, const uspg_coeff_opts *opts,
                         uspg_ctx **out);
 /* Frees the context and all its device memory (waits for its work first). */
@@ -168,15 +169,21 @@ uspg_status uspg_sync(uspg_ctx *ctx, uspg_stream stream);
 
 /* --- coefficients (Sec. III.A-C, Algorithm 1) -------------------------------- */
 
-/* Traces every ray of every representative view in FP64 (cylinder roots of
- * Eq. 3-4 formed as (mr-d)(mr+d), axial and radial plane crossings, midpoint
- * cell assignment of Eq. 5-10, pieces < 1e-9 of a cell dropped, repeated cells
- * merged) and stores the rows twice: ray-major for the forward ray sums and
- * cell-major for the correction.  Replaces any earlier store. */
+/* REPRESENTATIVES: traces every ray of every representative view in FP64
+ * (cylinder roots of Eq. 3-4 formed as (mr-d)(mr+d), axial and radial plane
+ * crossings, midpoint cell assignment of Eq. 5-10, pieces < 1e-9 of a cell
+ * dropped, repeated cells merged) and stores the rows twice: ray-major for the
+ * forward ray sums and cell-major for the correction.
+ * SEGMENTS: traces the first view's rays only, to their cylinder and
+ * axial-plane crossings (no radial planes, Sec. III.B), and stores each
+ * segment's ring, slab and end azimuths (64-bit fixed turns); an end azimuth
+ * within 2^-40 turn of a sector boundary counts as on it.
+ * Replaces any earlier store. */
 uspg_status uspg_build_coeffs(uspg_ctx *ctx, uspg_stream stream);
 uspg_status uspg_coeff_stats(const uspg_ctx *ctx, uspg_stats *out);
 /* Host copy of row `ray` of view `view` as the MART kernels see it (stored
- * representative row, sectors rotated to the view).  cells: host int64[cap],
+ * representative row, sectors rotated to the view; for the segment store the
+ * sectors the view's segments cover, weight 1).  cells: host int64[cap],
  * w: host double[cap] (the stored precision widened), *n = entries; if the
  * row is longer than cap, *n = its length and nothing is copied (EINVAL).
  * Synchronous. */
@@ -205,7 +212,10 @@ uspg_status uspg_get_image(const uspg_ctx *ctx, float *f, int32_t to_device, usp
  *   then each cell corrected once by the weighted geometric mean of its rays'
  *   ratios (P = 0 rays zero their cells).
  * With stop_tol > 0 (SEQUENTIAL), stops after the first sweep in which every
- * correction satisfies Eq. 19.  ENOTREADY without coefficients or projections. */
+ * correction satisfies Eq. 19.  ENOTREADY without coefficients or projections.
+ * A segment-store context serves SEQUENTIAL only (EUNSUPPORTED for PER_VIEW;
+ * likewise uspg_forward_project, uspg_autotune, uspg_mart_kernel_times,
+ * batches and server jobs, which read the representative store). */
 uspg_status uspg_mart(uspg_ctx *ctx, const uspg_mart_opts *opts, uspg_stream stream);
 /* Forward projection of one view with the current image (Eq. 17):
  * out = device float32 [rays]. */

@@ -96,3 +96,36 @@ def test_server_create_validates_on_host(U):
     with pytest.raises(U.UspgError) as e:
         U._check(U.lib().uspg_server_submit(None, None, None))
     assert e.value.status == U.EINVAL
+
+
+def test_create_validates_fan_scans_and_store_forms(U):
+    """Host-side checks of the fan geometry (Table 1) and of the coefficient
+    stores: a fan scan is 2D (n_v = 1, n_slabs = 1) with its source outside
+    the grid; the first-view segment store holds binary coefficients only."""
+    from paper_2208_12964_gb300 import synth
+
+    fan = synth.workload("2d-fan-128r-50v-101")
+    g, s, o, _ = U.descs_from_spec(fan)
+    U.uspg_destroy(U.uspg_create(g, s, o))
+    bad = []
+    g1, s1, o1, _ = U.descs_from_spec(fan)
+    s1.n_v = 2
+    bad.append((g1, s1, o1, "n_v"))
+    g2, s2, o2, _ = U.descs_from_spec(fan)
+    s2.src_to_axis = 0.5  # inside the disk
+    bad.append((g2, s2, o2, "src_to_det"))
+    g3, s3, o3, _ = U.descs_from_spec(fan)
+    o3.store_form = U.STORE_SEGMENTS  # with length weights
+    bad.append((g3, s3, o3, "binary"))
+    g4, s4, o4, _ = U.descs_from_spec(fan)
+    o4.store_form = 7
+    bad.append((g4, s4, o4, "store_form"))
+    for g_, s_, o_, word in bad:
+        with pytest.raises(U.UspgError) as e:
+            U.uspg_create(g_, s_, o_)
+        assert e.value.status == U.EINVAL
+        assert word in U.uspg_last_error(None)
+    seg = synth.workload("2d-fan-128r-50v-101-segments")
+    g5, s5, o5, _ = U.descs_from_spec(seg)
+    assert o5.weight_mode == U.BINARY and o5.store_form == U.STORE_SEGMENTS
+    U.uspg_destroy(U.uspg_create(g5, s5, o5))
