@@ -449,6 +449,22 @@ enum { kSegGlobal = 0, kSegSmem = 1, kSegSplit = 2 };
 // with unit coefficients) and after the warp sum correct every cell by
 // (P/Pbar)^lambda or 1 - lambda (1 - P/Pbar) (Eq. 18).
 constexpr int kSegSlots = 8;  // segments per lane held in registers (rays of up to 256 segments)
+constexpr int kSegUnroll = 4;  // cells of a segment read together (most segments have 1-3)
+
+// Sum of the image over a segment's cells: kSegUnroll independent loads at a time.
+template <class Img>
+__device__ __forceinline__ float seg_sum(const SegCells &sc, int dir, const Img &F)
+{
+    float acc = 0.0f;
+    for (int t0 = 0; t0 < sc.n; t0 += kSegUnroll) {
+        float v[kSegUnroll];
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; u++) v[u] = t0 + u < sc.n ? *F(seg_cell(sc, dir, t0 + u)) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; u++) acc += v[u];
+    }
+    return acc;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(32) k_seq_seg(const long long *__restrict__ ptr, const uint64_t *__restrict__ fa,
@@ -507,7 +523,7 @@ __global__ void __launch_bounds__(32) k_seq_seg(const long long *__restrict__ pt
                     if (i < ns) {
                         int back = seg_back(rs[b + i]);
                         if (back) seg_dedup(reg[c], dir, ends[i - back]);
-                        for (int t = 0; t < reg[c].n; t++) acc += *F(seg_cell(reg[c], dir, t));
+                        acc += seg_sum(reg[c], dir, F);
                     }
                 }
                 for (int i = kSegSlots * 32 + lane; i < ns; i += 32) {
@@ -515,7 +531,7 @@ __global__ void __launch_bounds__(32) k_seq_seg(const long long *__restrict__ pt
                     uint32_t x = rs[q];
                     SegCells sc = seg_range(fa, fb, x, rt, cps, q, T, nudge, dir);
                     if (seg_back(x)) seg_dedup(sc, dir, ends[i - seg_back(x)]);
-                    for (int t = 0; t < sc.n; t++) acc += *F(seg_cell(sc, dir, t));
+                    acc += seg_sum(sc, dir, F);
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -523,11 +539,22 @@ __global__ void __launch_bounds__(32) k_seq_seg(const long long *__restrict__ pt
                     float ratio = p / acc;
                     float fac = rule == USPG_LINEAR_EQ18 ? 1.0f - lambda * (1.0f - ratio) : powf(ratio, lambda);
                     auto upd = [&](const SegCells &sc) {
-                        for (int t = 0; t < sc.n; t++) {
-                            float *fp = F(seg_cell(sc, dir, t));
-                            float old = *fp, nv = old * fac;
-                            if (tol > 0.0f && fabsf(nv - old) > tol * fabsf(old)) changed = 1;
-                            *fp = nv;
+                        for (int t0 = 0; t0 < sc.n; t0 += kSegUnroll) {
+                            float *fp[kSegUnroll];
+                            float old[kSegUnroll];
+#pragma unroll
+                            for (int u = 0; u < kSegUnroll; u++) {
+                                fp[u] = F(seg_cell(sc, dir, t0 + u < sc.n ? t0 + u : t0));
+                                old[u] = *fp[u];
+                            }
+#pragma unroll
+                            for (int u = 0; u < kSegUnroll; u++) {
+                                if (t0 + u < sc.n) {
+                                    float nv = old[u] * fac;
+                                    if (tol > 0.0f && fabsf(nv - old[u]) > tol * fabsf(old[u])) changed = 1;
+                                    *fp[u] = nv;
+                                }
+                            }
                         }
                     };
 #pragma unroll
