@@ -131,6 +131,56 @@ def test_rows_3d_cone_full_size_sampled(torch_cuda):
         assert_rows_equal(gc, gw, oc, ow, TOL_W, where=f"view {k} ray {ray}")
 
 
+def test_cone256_full_size(torch_cuda):
+    """The 256-ring, 256-slab, 180-view cone with a 512x512 detector, built as
+    bench.py builds it.  FP16 store: 200 sampled rows against the oracle's
+    direct trace (index lists exact; each weight the FP64 length rounded once
+    to FP16 in units of the cell size).  FP32 store: one per-view step of
+    view 0 from f0 = 1 over all 50.5 M cells against the oracle's step."""
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.workload("3d-cone-256r-256s-180v-512")
+    o = oracle_for(spec)
+    o.set_threads(16)
+    g = Gpu(spec, dtype=uspg.F16).build()
+    st = g.stats()
+    assert st["n_reps"] == 30 and st["n_cells"] == 50528256 and st["mirrored"] == 1
+    unit = min(spec["r"], spec["h"])
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        k, ray = int(rng.integers(180)), int(rng.integers(512 * 512))
+        gc, gw = g.row(k, ray)
+        oc, ow = o.row(k, ray)
+        assert np.array_equal(gc, oc), f"view {k} ray {ray}"
+        big = ow > 1e-4 * unit
+        if big.any():
+            assert np.max(np.abs(gw[big] - ow[big]) / ow[big]) <= 2 ** -10
+    g.close()
+    # view 0's projections (noise-free line integrals); no other view is used
+    S, D = synth.ray_endpoints(spec, 0)
+    proj = np.zeros((180, 512 * 512), np.float32)
+    proj[0] = synth.line_integrals(synth.phantom_for(spec), S, D, planar=False)
+    g = Gpu(spec).build()
+    U = g.U
+    U.uspg_set_projections(g.ctx, proj, False)
+    U.uspg_fill_image(g.ctx, 1.0)
+    U.uspg_autotune(g.ctx)
+    opts, keep = U.mart_opts(1, 0.1, U.PER_VIEW, view_steps=1)
+    U.uspg_mart(g.ctx, opts)
+    U.uspg_sync(g.ctx)
+    got = np.zeros(o.n_cells, np.float32)
+    U.uspg_get_image(g.ctx, got, False)
+    g.close()
+    ref = np.ones(o.n_cells)
+    o.mart_views_sample(proj, ref, [0], 0.1)
+    hit = ref != 1.0
+    assert hit.sum() > 0.5 * o.n_cells
+    assert np.all(got[~hit] == 1.0)
+    nz = ref > 0
+    assert np.all(got[~nz] == 0.0)
+    assert np.max(np.abs(got[nz] - ref[nz]) / ref[nz]) < 2e-5
+
+
 def test_binary_weights(torch_cuda):
     from paper_2208_12964_gb300 import uspg
 
