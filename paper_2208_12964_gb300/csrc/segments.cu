@@ -490,24 +490,32 @@ __global__ void __launch_bounds__(32) k_seq_seg(const long long *__restrict__ pt
             const uint64_t T = turns[k];
             const float *pk = proj + (long long)k * n_rays;
             long long nb = ptr[0], ne = ptr[1];
+            int ndir = sdir[0];
+            float np = pk[0];
             for (int ray = 0; ray < n_rays; ray++) {
                 long long b = nb, e = ne;
-                int dir = sdir[ray];
-                float p = pk[ray];
-                if (ray + 1 < n_rays) {  // bounds of the next ray in flight
+                int dir = ndir;
+                float p = np;
+                if (ray + 1 < n_rays) {  // bounds, turn and projection of the next ray in flight
                     nb = e;
                     ne = ptr[ray + 2];
+                    ndir = sdir[ray + 1];
+                    np = pk[ray + 1];
                 }
                 if (e == b) continue;
                 const int ns = (int)(e - b);
                 SegCells reg[kSegSlots];
+                int bk[kSegSlots];  // shared-cell links of the slots
                 // sector ranges; each segment's last sector for the shared-cell rule
 #pragma unroll
                 for (int c = 0; c < kSegSlots; c++) {
                     int i = c * 32 + lane;
+                    bk[c] = 0;
                     if (i < ns) {
                         long long q = b + i;
-                        reg[c] = seg_range(fa, fb, rs[q], rt, cps, q, T, nudge, dir);
+                        uint32_t x = rs[q];
+                        bk[c] = seg_back(x);
+                        reg[c] = seg_range(fa, fb, x, rt, cps, q, T, nudge, dir);
                         ends[i] = seg_end(reg[c], dir);
                     }
                 }
@@ -521,8 +529,7 @@ __global__ void __launch_bounds__(32) k_seq_seg(const long long *__restrict__ pt
                 for (int c = 0; c < kSegSlots; c++) {
                     int i = c * 32 + lane;
                     if (i < ns) {
-                        int back = seg_back(rs[b + i]);
-                        if (back) seg_dedup(reg[c], dir, ends[i - back]);
+                        if (bk[c]) seg_dedup(reg[c], dir, ends[i - bk[c]]);
                         acc += seg_sum(reg[c], dir, F);
                     }
                 }
