@@ -541,3 +541,37 @@ def test_segment_store_mart_equals_direct_binary_mart():
     a, _ = o.mart_sequential(proj, f0, 3, 0.4, rule=oracle.LINEAR_EQ18)
     b, _ = os_.mart_sequential(proj, f0, 3, 0.4, rule=oracle.LINEAR_EQ18)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["fan", "cone"])
+def test_quarter_symmetry_of_first_view_lines(case):
+    """Sec. III.C: reflections of the first view's lines in the transverse
+    plane (u -> -u, y -> -y) and, for a centred cone scan, in the axial
+    mid-plane (v -> -v, z -> -z) give the other lines' crossings, so a quarter
+    of the lines determine all.  The mirror line has the same segments (ring,
+    length) with negated azimuths and reversed turn, or with mirrored slabs."""
+    if case == "fan":
+        spec = fan2d(16, 1, 41, 0.05)
+    else:
+        spec = cone3d(8, 6, 1, 16)
+    o = _binary(spec)
+    n_u, n_v = spec["n_u"], spec["n_v"]
+    n_s = spec["n_slabs"] if case == "cone" else 1
+    window = 1 << 24  # fixed-turn units: rounding of the two atan2 evaluations stays far inside
+    for ray in range(o.n_rays):
+        a, c = ray % n_u, ray // n_u
+        rg, sb, fa, fb, ln, dr = o.segments(ray)
+        mu = c * n_u + (n_u - 1 - a)  # transverse mirror
+        rg2, sb2, fa2, fb2, ln2, dr2 = o.segments(mu)
+        assert np.array_equal(rg, rg2) and np.array_equal(sb, sb2) and dr2 == -dr
+        assert np.allclose(ln, ln2, rtol=1e-12, atol=1e-15)
+        for x, y in ((fa, fa2), (fb, fb2)):
+            s = (x.astype(object) + y.astype(object)) % (1 << 64)  # -F mod 2^64 plus F
+            assert all(min(int(v), (1 << 64) - int(v)) < window for v in s)
+        if case == "cone":
+            mv = (n_v - 1 - c) * n_u + a  # axial mirror
+            rg3, sb3, fa3, fb3, ln3, dr3 = o.segments(mv)
+            assert np.array_equal(rg, rg3) and np.array_equal(sb, n_s - 1 - sb3) and dr3 == dr
+            assert np.allclose(ln, ln3, rtol=1e-12, atol=1e-15)
+            assert all(min(int((x - y) % (1 << 64)), int((y - x) % (1 << 64))) < window
+                       for x, y in zip(fa.tolist(), fa3.tolist()))
