@@ -16,6 +16,9 @@
  *     cell assignment [Sec. III.B, Eq. 5-10], length weights
  *   - the view-0 store reused by rotation [Sec. III.B-C], as an in-oracle
  *     check that rotated rows equal directly traced rows
+ *   - the first view's segment store of binary coefficients, re-binned to
+ *     each view by adding its source angle [Sec. III.B-C, Algorithm 1]
+ *   - scans: parallel-beam 2D, fan-beam 2D [Table 1], cone-beam 3D
  *   - MART, ray-sequential and per-view simultaneous [Sec. III.D, Eq. 17-19]
  *   - USPG -> Cartesian resampling [Sec. II.B]
  *
