@@ -486,6 +486,7 @@ uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t 
         if (st) return st;
         *n = (int32_t)cl.size();
         if ((long long)cl.size() > cap) return fail(c, USPG_EINVAL, "row longer than cap");
+        if (!cells || !w) return cl.empty() ? USPG_OK : fail(c, USPG_EINVAL, "NULL cells or w");
         for (size_t q = 0; q < cl.size(); q++) {
             cells[q] = cl[q];
             w[q] = 1.0;
