@@ -5,9 +5,10 @@
 //
 // Usage: host_walk geometry n_rings n_slabs sector_rule r h z_min n_views
 //                  arc_num arc_den n_u n_v du dv d_so d_sd view ray_begin ray_end
-// Output, one line per ray: "ray n cell_0 w_0 cell_1 w_1 ..." with global
-// cell ids (slab * cells_per_slab + head + sector) and FP64 lengths
-// (%.17g), entries in the walk's order.
+// Output, one line per ray: "ray bound n cell_0 w_0 cell_1 w_1 ..." with the
+// FP32 sizing pass's bound on the row's length (size_ray), then the walk's
+// entries: global cell ids (slab * cells_per_slab + head + sector) and FP64
+// lengths (%.17g), in the walk's order.
 #include <math.h>  // the walk calls cos, sin, sqrt, floor, atan2 unqualified
 
 #include "../paper_2208_12964_gb300/csrc/walk.cuh"
@@ -83,7 +84,7 @@ int main(int argc, char **argv)
         sink.root = root.data();
         walk_ray(g, rt.data(), bdir.data(), bdirf.data(), view, ray, sink, &status);
         if (sink.overflow) status |= kStatusCountMismatch;
-        std::printf("%d %d", ray, sink.n);
+        std::printf("%d %d %d", ray, size_ray(g, rt.data(), bdirf.data(), view, ray), sink.n);
         for (int q = 0; q < sink.n; q++) {
             uint32_t pc = idx[q];
             long long cell = (long long)cell_slab(pc) * g.cells_per_slab + rt[cell_ring(pc)].head + cell_sector(pc);

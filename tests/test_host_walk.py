@@ -9,8 +9,9 @@ rounded FP64 operations and the same libm, but where a radial crossing falls
 on a circle crossing to within rounding the oracle, which splits the whole
 line at every crossing, can start the next piece one unit in the last place
 later than the walk, which splits each ring segment at the crossings inside
-it).  This checks the generator's logic on every row of small scans
-and on sampled rows of the full-size cone, independently of a GPU run.
+it).  Every row must also fit the FP32 sizing pass's bound (size_ray).  This
+checks the generator's logic on every row of small scans and on blocks of
+rows of the full-size cone, independently of a GPU run.
 """
 import os
 import shutil
@@ -56,9 +57,12 @@ def host_rows(walker, spec, view, rays):
     rows = {}
     for line in r.stdout.splitlines():
         t = line.split()
-        n = int(t[1])
-        cells = np.array(t[2:2 + 2 * n:2], np.int64)
-        w = np.array(t[3:3 + 2 * n:2], np.float64)
+        bound, n = int(t[1]), int(t[2])
+        # the FP32 sizing pass bounds every row the FP64 walk writes (rays
+        # through the axis included: the centre bins of odd detectors)
+        assert n <= bound, f"view {view} ray {t[0]}: {n} entries > bound {bound}"
+        cells = np.array(t[3:3 + 2 * n:2], np.int64)
+        w = np.array(t[4:4 + 2 * n:2], np.float64)
         o = np.argsort(cells, kind="stable")
         rows[int(t[0])] = (cells[o], w[o])
     return rows
