@@ -110,3 +110,18 @@ def test_host_walk_full_size_cone_blocks(walker):
     in three views."""
     spec = synth.workload("3d-cone-128r-128s-90v-256")
     compare(walker, spec, (0, 7, 44), blocks=[(127 * 256, 129 * 256), (230 * 256, 231 * 256)])
+
+
+def test_host_walk_paper_grid_parallel_every_row(walker):
+    """Eq. 1's grid, n_g = 4(2n-1) (the one the bijective resample needs),
+    parallel scan over a full turn with an even bin count."""
+    spec = synth.parallel_workload(24, 20, 48, arc=(1, 1), sector_rule=synth.SECT_4_2N1)
+    compare(walker, spec, range(20))
+
+
+def test_host_walk_off_centre_cone_every_row(walker):
+    """A slab stack off the source plane (no z-mirror: rows above and below the
+    mid-plane differ), odd detector."""
+    spec = synth.cone_workload(10, 8, 12, 21, noise=False)
+    spec["z_min"] = -0.75
+    compare(walker, spec, range(12))
