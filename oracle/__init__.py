@@ -91,7 +91,7 @@ def _load():
             L.orc_mart_sequential.restype = C.c_int32
             L.orc_mart_sequential.argtypes = [V, V, V, C.c_int32, C.c_double, C.c_int32, C.c_double]
             L.orc_mart_per_view.restype = C.c_int32
-            L.orc_mart_per_view.argtypes = [V, V, V, C.c_int32, C.c_double, V]
+            L.orc_mart_per_view.argtypes = [V, V, V, C.c_int32, C.c_double, V, C.c_int32, C.c_double]
             L.orc_mart_views_sample.restype = C.c_int64
             L.orc_mart_views_sample.argtypes = [V, V, V, V, C.c_int32, C.c_double]
             L.orc_resample_point.argtypes = [V, V, C.c_int32, C.c_int32, V]
@@ -211,15 +211,19 @@ class Oracle:
         n = self.L.orc_mart_sequential(self._h, _ptr(proj), _ptr(f), int(iters), float(lam), int(rule), float(tol))
         return f, int(n)
 
-    def mart_per_view(self, proj, f0, iters, lam, order=None):
+    def mart_per_view(self, proj, f0, iters, lam, order=None, rule=POWER, tol=0.0, return_sweeps=False):
+        """Per-view simultaneous MART (geometric-mean POWER or arithmetic-mean
+        LINEAR_EQ18 combination of the view's rays, Eq. 18), up to ``iters``
+        sweeps, stopping early by Eq. 19 when ``tol`` > 0.  Returns the image,
+        or (image, sweeps run) with ``return_sweeps``."""
         proj = np.ascontiguousarray(proj, np.float32).reshape(-1)
         f = np.array(f0, np.float64, copy=True).reshape(-1)
         o = None
         if order is not None:
             o = np.ascontiguousarray(order, np.int32)
-        self.L.orc_mart_per_view(self._h, _ptr(proj), _ptr(f), int(iters), float(lam),
-                                 _ptr(o) if o is not None else None)
-        return f
+        n = self.L.orc_mart_per_view(self._h, _ptr(proj), _ptr(f), int(iters), float(lam),
+                                     _ptr(o) if o is not None else None, int(rule), float(tol))
+        return (f, int(n)) if return_sweeps else f
 
     def mart_views_sample(self, proj, f, views, lam):
         """One per-view step for each view in ``views`` (f updated in place);

@@ -19,7 +19,8 @@
  *   - the first view's segment store of binary coefficients, re-binned to
  *     each view by adding its source angle [Sec. III.B-C, Algorithm 1]
  *   - scans: parallel-beam 2D, fan-beam 2D [Table 1], cone-beam 3D
- *   - MART, ray-sequential and per-view simultaneous [Sec. III.D, Eq. 17-19]
+ *   - MART, ray-sequential and per-view simultaneous, power rule or Eq. 18,
+ *     Eq. 19 stopping [Sec. III.D, Eq. 17-19]
  *   - USPG -> Cartesian resampling [Sec. II.B]
  *
  * Readings of the paper taken here (each is listed with its reason in the
@@ -38,10 +39,14 @@
  *     Sec. III.B); a cell entered twice gets the sum of its pieces
  *
  * Parity status: every function below is pinned by tests against closed
- * forms, brute-force point sampling or values printed in the paper, except
- * the square-ring ordering of the bijective resample, whose figure (Fig. 3)
- * is missing from the paper: "parity unpinned" beyond "is a permutation that
- * keeps each ring's cells on the matching square ring".
+ * forms, brute-force point sampling or values printed in the paper.  The
+ * square-ring ordering of the bijective resample rests on a reading, because
+ * the figure that fixes it (Fig. 3) is missing from the paper: it is pinned
+ * against pixel orders listed by hand from that reading (counter-clockwise
+ * from +x) and against azimuth monotonicity, not against the paper itself.
+ * The per-view combination of several rays' corrections (geometric mean for
+ * the power rule, arithmetic mean for Eq. 18) is likewise a reading: pinned
+ * by closed forms of that reading.
  */
 #include <math.h>
 #include <stdint.h>
@@ -931,14 +936,21 @@ int32_t orc_mart_sequential(const orc_ctx *c, const float *proj, double *f, int3
     return it;
 }
 
-/* One per-view simultaneous MART step for view k: all ray sums of the view
- * are formed with the current image, then every cell v hit by a ray with
- * P_bar > 0 is corrected once by the weighted geometric mean of the ratios
- *   f_v *= exp(lambda * sum_l alpha_lv ln(P_l/P_bar_l) / sum_l alpha_lv),
- * and a cell hit by such a ray with P_l = 0 is set to 0 (the limit of the
- * same product).  Cells not hit keep their value. */
-static void view_step(const orc_ctx *c, const orc_rows *R, int32_t k, const float *proj, double *f,
-                      double lambda, double *num, double *den, unsigned char *zero)
+/* One per-view simultaneous MART step for view k (Sec. III.D): all ray sums
+ * P_bar_l of the view are formed with the current image (Eq. 17), then every
+ * cell v met by a ray with P_bar_l > 0 is corrected once, combining the
+ * corrections the view's rays l would make one by one:
+ *   POWER:       the weighted geometric mean of the ratios,
+ *                f_v *= exp(lambda * sum_l alpha_lv ln(P_l/P_bar_l) / sum_l alpha_lv);
+ *                a cell met by such a ray with P_l = 0 is set to 0 (the limit
+ *                of the same product);
+ *   LINEAR_EQ18: the weighted arithmetic mean of the factors of Eq. 18,
+ *                f_v *= sum_l alpha_lv (1 - lambda (1 - P_l/P_bar_l)) / sum_l alpha_lv
+ *                (lambda is the relaxation beta; P_l = 0 gives 1 - beta).
+ * Cells met by no such ray keep their value.  Returns 1 if tol > 0 and some
+ * correction breaks Eq. 19, |f_new - f_old| <= tol |f_old|; else 0. */
+static int view_step(const orc_ctx *c, const orc_rows *R, int32_t k, const float *proj, double *f,
+                     double lambda, int32_t rule, double tol, double *num, double *den, unsigned char *zero)
 {
     int32_t nr = c->n_rays;
     memset(num, 0, sizeof(double) * c->n_cells);
@@ -956,6 +968,14 @@ static void view_step(const orc_ctx *c, const orc_rows *R, int32_t k, const floa
     for (int32_t i = 0; i < nr; i++) {
         if (R->ptr[i] == R->ptr[i + 1] || !(s[i] > 0.0)) continue;
         double P = (double)proj[(int64_t)k * nr + i];
+        if (rule == OR_LINEAR_EQ18) {
+            double fac = 1.0 - lambda * (1.0 - P / s[i]);
+            for (int64_t q = R->ptr[i]; q < R->ptr[i + 1]; q++) {
+                num[R->cell[q]] += R->w[q] * fac;
+                den[R->cell[q]] += R->w[q];
+            }
+            continue;
+        }
         if (P == 0.0) {
             for (int64_t q = R->ptr[i]; q < R->ptr[i + 1]; q++) {
                 zero[R->cell[q]] = 1;
@@ -969,37 +989,54 @@ static void view_step(const orc_ctx *c, const orc_rows *R, int32_t k, const floa
             den[R->cell[q]] += R->w[q];
         }
     }
+    int moved = 0;
     for (int64_t v = 0; v < c->n_cells; v++) {
-        if (zero[v])
-            f[v] = 0.0;
-        else if (den[v] > 0.0)
-            f[v] *= exp(lambda * num[v] / den[v]);
+        if (!(den[v] > 0.0)) continue;
+        double old = f[v], nw;
+        if (rule == OR_LINEAR_EQ18)
+            nw = old * (num[v] / den[v]);
+        else if (zero[v])
+            nw = 0.0;
+        else
+            nw = old * exp(lambda * num[v] / den[v]);
+        if (tol > 0.0 && fabs(nw - old) > tol * fabs(old)) moved = 1;
+        f[v] = nw;
     }
     free(s);
+    return moved;
 }
 
-/* Per-view simultaneous MART: `iters` sweeps over the views in the order
- * `order` (NULL = 0..p-1).  Rows are traced once per view per sweep. */
+/* Per-view simultaneous MART: up to `iters` sweeps over the views in the
+ * order `order` (NULL = 0..p-1), each view one step of view_step with the
+ * update `rule`.  If tol > 0 the iteration stops after the first sweep in
+ * which every correction satisfies Eq. 19.  Rows are traced once per view per
+ * sweep.  Returns the sweeps run. */
 int32_t orc_mart_per_view(const orc_ctx *c, const float *proj, double *f, int32_t iters, double lambda,
-                          const int32_t *order)
+                          const int32_t *order, int32_t rule, double tol)
 {
     const orc_problem *p = &c->p;
     double *num = (double *)malloc(sizeof(double) * c->n_cells);
     double *den = (double *)malloc(sizeof(double) * c->n_cells);
     unsigned char *zero = (unsigned char *)malloc(c->n_cells);
-    for (int32_t it = 0; it < iters; it++) {
+    int32_t it;
+    for (it = 0; it < iters; it++) {
+        int moved = 0;
         for (int32_t q = 0; q < p->n_views; q++) {
             int32_t k = order ? order[q] : q;
             orc_rows R;
             rows_build(c, k, &R);
-            view_step(c, &R, k, proj, f, lambda, num, den, zero);
+            moved |= view_step(c, &R, k, proj, f, lambda, rule, tol, num, den, zero);
             rows_free(&R);
+        }
+        if (tol > 0.0 && !moved) {
+            it++;
+            break;
         }
     }
     free(num);
     free(den);
     free(zero);
-    return iters;
+    return it;
 }
 
 /* Same as orc_mart_per_view but over the views listed in `views` only, one
@@ -1015,7 +1052,7 @@ int64_t orc_mart_views_sample(const orc_ctx *c, const float *proj, double *f, co
         orc_rows R;
         rows_build(c, views[q], &R);
         nnz += R.ptr[c->n_rays];
-        view_step(c, &R, views[q], proj, f, lambda, num, den, zero);
+        view_step(c, &R, views[q], proj, f, lambda, OR_POWER, 0.0, num, den, zero);
         rows_free(&R);
     }
     free(num);

@@ -351,6 +351,89 @@ def test_per_view_zero_projection_zeroes_cells_and_skips_empty():
     assert np.all(np.isfinite(f)) and np.all(f >= 0)
 
 
+def test_per_view_linear_eq18_one_cell_closed_form():
+    """Per-view form of Eq. 18 on one cell met by three rays of one view
+    (u = -2/3, 0, 2/3: chords 2 sqrt(5)/3, 2, 2 sqrt(5)/3): the cell's factor
+    is the weighted arithmetic mean of the rays' factors 1 - beta (1 - P/Pbar),
+    weights the rays' chords.  A ray with P = 0 contributes 1 - beta (it does
+    not zero the cell, unlike the power form); the power form's geometric mean
+    is checked on the same rays."""
+    o = oracle.Oracle(_one_cell(views=1, bins=3))
+    w = np.array([2 * math.sqrt(5) / 3, 2.0, 2 * math.sqrt(5) / 3])
+    for b in range(3):
+        assert abs(o.row(0, b)[1][0] - w[b]) < 1e-14
+    f0, beta = 1.2, 0.35
+    for pv in ((0.9, 0.4, 1.3), (0.0, 0.7, 1.1)):
+        p = np.array([pv], np.float32)
+        q = p[0].astype(np.float64)
+        fac = 1.0 - beta * (1.0 - q / (w * f0))
+        want = f0 * float(np.sum(w * fac) / np.sum(w))
+        got = o.mart_per_view(p, [f0], 1, beta, rule=oracle.LINEAR_EQ18)
+        assert abs(got[0] - want) < 1e-14
+    p = np.array([[0.9, 0.4, 1.3]], np.float32)
+    q = p[0].astype(np.float64)
+    want = f0 * math.exp(beta * float(np.sum(w * np.log(q / (w * f0))) / np.sum(w)))
+    assert abs(o.mart_per_view(p, [f0], 1, beta)[0] - want) < 1e-14
+
+
+def test_per_view_two_ring_closed_form_both_rules():
+    """Two one-sector rings, two off-centre rays (u = -1/4, +1/4) of one view:
+    both rays cross both cells with weights (inner chord, outer chord minus
+    inner); each cell is corrected once from both rays' ratios, by the
+    geometric (POWER) or arithmetic (Eq. 18) weighted mean."""
+    spec = dict(par2d(2, views=1, bins=2, rule=oracle.SECT_CUSTOM, custom=[1, 1]), du=0.5)
+    o = oracle.Oracle(spec)
+    u, r = 0.25, 0.5
+    w_in = 2 * math.sqrt(r * r - u * u)
+    w_out = 2 * math.sqrt(1.0 - u * u) - w_in
+    wv = np.array([w_in, w_out])
+    f0 = np.array([0.8, 1.7])
+    p = np.array([[1.1, 0.6]], np.float32)
+    s = np.array([wv @ f0, wv @ f0])  # both rays have the same weights
+    ratio = np.array([float(p[0, 0]), float(p[0, 1])]) / s
+    lam = 0.3
+    # every cell sees both rays with its own weight, so its weights cancel in the mean
+    geo = f0 * np.exp(lam * np.mean(np.log(ratio)))
+    lin = f0 * np.mean(1.0 - lam * (1.0 - ratio))
+    assert np.allclose(o.mart_per_view(p, f0, 1, lam), geo, rtol=1e-14)
+    assert np.allclose(o.mart_per_view(p, f0, 1, lam, rule=oracle.LINEAR_EQ18), lin, rtol=1e-14)
+
+
+def test_per_view_eq19_stopping_and_linear_fixed_point():
+    """Eq. 19 in the per-view schedule: consistent data p = A f* leaves f*
+    in place (ratio 1: both rules give factor 1), so the first sweep meets a
+    tolerance of 1e-3 and the run stops after it; from f = 1 a tolerance of
+    1e-9 is never met and every sweep runs."""
+    spec = par2d(3, views=4, bins=7)
+    o = oracle.Oracle(spec)
+    rng = np.random.default_rng(5)
+    fstar = 0.5 + rng.random(o.n_cells)
+    p = np.stack([o.forward(k, fstar) for k in range(4)]).astype(np.float32)
+    for rule in (oracle.POWER, oracle.LINEAR_EQ18):
+        f, n = o.mart_per_view(p, fstar, 50, 0.5, rule=rule, tol=1e-3, return_sweeps=True)
+        assert n == 1 and np.max(np.abs(f / fstar - 1)) < 1e-6
+        _, n = o.mart_per_view(p, np.ones(o.n_cells), 7, 0.5, rule=rule, tol=1e-9, return_sweeps=True)
+        assert n == 7
+        _, n = o.mart_per_view(p, np.ones(o.n_cells), 7, 0.5, rule=rule, return_sweeps=True)
+        assert n == 7
+
+
+def test_per_view_linear_reduces_misfit():
+    spec = par2d(6, views=12, bins=13, arc=(1, 2))
+    o = oracle.Oracle(spec)
+    fstar = 0.2 + np.random.default_rng(4).random(o.n_cells)
+    p = np.stack([o.forward(k, fstar) for k in range(12)]).astype(np.float32)
+
+    def misfit(f):
+        return sum(np.sum((o.forward(k, f) - p[k]) ** 2) for k in range(12))
+
+    f0 = np.ones(o.n_cells)
+    f1 = o.mart_per_view(p, f0, 2, 0.5, rule=oracle.LINEAR_EQ18)
+    f2 = o.mart_per_view(p, f0, 10, 0.5, rule=oracle.LINEAR_EQ18)
+    assert misfit(f2) < misfit(f1) < misfit(f0)
+    assert np.all(f2 > 0)
+
+
 def test_fixed_point_of_consistent_data():
     """p = A f* (rounded to float32) leaves f* unchanged up to that rounding."""
     spec = par2d(6, views=8, bins=13, arc=(1, 2))
@@ -432,6 +515,44 @@ def test_resample_bijection_is_ring_preserving_permutation():
     assert np.array_equal(ring + 1, sq.astype(int))
     with pytest.raises(ValueError):
         oracle.Oracle(par2d(3)).resample_bijection(np.zeros(36))
+
+
+def test_resample_bijection_order_hand_listed():
+    """The pixel order of the one-to-one map for N = 1, 2, 3 against lists
+    written by hand from the reading of Sec. II.A-B (both rings numbered
+    counter-clockwise from +x; tests/golden/bijection_order.json): a
+    clockwise walk, or one starting a pixel off, fails here."""
+    gold = json.load(open(os.path.join(GOLD, "bijection_order.json")))["lists"]
+    for N_s, rings in gold.items():
+        N = int(N_s)
+        o = oracle.Oracle(par2d(N, rule=oracle.SECT_4_2N1))
+        ng, head = o.grid_tables()
+        ids = o.resample_bijection(np.arange(o.n_cells, dtype=np.float64))[0]
+        assert len(rings) == N
+        for n, pix in enumerate(rings, start=1):
+            assert len(pix) == ng[n - 1] == 8 * n - 4
+            for j, (a, b) in enumerate(pix):
+                assert ids[b, a] == head[n - 1] + j, (N, n, j)
+
+
+@pytest.mark.parametrize("N", [4, 7, 16])
+def test_resample_bijection_azimuth_order(N):
+    """Within every square ring the cell index H_n + j grows with the
+    pixel-centre azimuth measured counter-clockwise from +x in [0, 2 pi), and
+    j = 0 is the pixel with the smallest azimuth (the first at or above +x)."""
+    o = oracle.Oracle(par2d(N, rule=oracle.SECT_4_2N1))
+    ng, head = o.grid_tables()
+    ids = o.resample_bijection(np.arange(o.n_cells, dtype=np.float64))[0].astype(np.int64)
+    c = np.arange(2 * N) - N + 0.5
+    X, Y = np.meshgrid(c, c)  # X[b, a] = a - N + 1/2, Y[b, a] = b - N + 1/2
+    az = np.mod(np.arctan2(Y, X), 2 * math.pi)
+    for n in range(1, N + 1):
+        sel = (ids >= head[n - 1]) & (ids < head[n - 1] + ng[n - 1])
+        j = ids[sel] - head[n - 1]
+        order = np.argsort(j)
+        a_sorted = az[sel][order]
+        assert np.all(np.diff(a_sorted) > 0), n
+        assert j[np.argmin(az[sel])] == 0
 
 
 # ----------------------------------------------------------------- inputs ---
