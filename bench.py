@@ -187,13 +187,12 @@ def run_ours(args, rank, world, local):
         uspg.uspg_resample_cartesian(ctx, uspg.RESAMPLE_POINT, nx, ny, img_dev, True, sp)
 
     def step_e2e():
+        # host projections in, host image out, both through the C ABI
         uspg.uspg_set_projections(ctx, proj_pin, False, sp)
         uspg.uspg_build_coeffs(ctx, sp)
         uspg.uspg_fill_image(ctx, 1.0, sp)
         uspg.uspg_mart(ctx, opts, sp)
-        uspg.uspg_resample_cartesian(ctx, uspg.RESAMPLE_POINT, nx, ny, img_dev, True, sp)
-        with torch.cuda.stream(stream):
-            img_pin.copy_(img_dev, non_blocking=True)
+        uspg.uspg_resample_cartesian(ctx, uspg.RESAMPLE_POINT, nx, ny, img_pin, False, sp)
 
     def barrier():
         if world > 1:
@@ -304,21 +303,30 @@ def latency_line(info):
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_cone128_mart.json")
 
 
+def sources_sha256(files) -> str:
+    """SHA-256 over the given repository files, in order."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def sources_hash_matches(rec: dict) -> bool:
+    return sources_sha256(rec["sources"]) == rec["sources_sha256"]
+
+
 def measured_traffic(kernel: str, dtype: str, mirrored: bool, spec: dict):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
     None when there is no capture for this form or the kernel sources have
     changed since it was taken (checked by hash)."""
-    import hashlib
-
     try:
         rec = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
-    h = hashlib.sha256()
-    for f in rec["sources"]:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest() != rec["sources_sha256"]:
+    if not sources_hash_matches(rec):
         return None
     geo = f"{spec['n_rings']}r-{spec['n_slabs'] if spec['geometry'] == 1 else 1}s-{spec['n_u']}x{spec['n_v']}"
     k = rec["kernels"].get(f"{geo}/{kernel}/{dtype}/{'mirrored' if mirrored else 'full'}")
@@ -689,7 +697,9 @@ def main():
     ms_step = info["t_ms"] / K
     value = info["updates_per_step"] * K * world / (info["t_ms"] * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
-            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f32" if args.coeff_dtype == "f32" else
+                      f"{args.coeff_dtype} coefficients, f32 accumulation and image"),
             "data": "synthetic",
             "config": {"workload": args.workload, "rings": info["spec"]["n_rings"],
                        "slabs": info["spec"]["n_slabs"] if info["spec"]["geometry"] == 1 else 1,

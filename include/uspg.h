@@ -76,7 +76,10 @@ enum { USPG_STORE_REPRESENTATIVES = 0, USPG_STORE_SEGMENTS = 1 };
 enum { USPG_F32 = 0, USPG_F16 = 1, USPG_BF16 = 2 };
 /* MART schedules (Sec. III.D) */
 enum { USPG_SEQUENTIAL = 0, USPG_PER_VIEW = 1 };
-/* update rules: POWER f *= (P/Pbar)^(lambda w/max w); LINEAR_EQ18 f *= 1 - lambda (1 - P/Pbar) */
+/* update rules (Sec. III.D).  Ray-sequential: POWER f *= (P/Pbar)^(lambda w/max w),
+ * LINEAR_EQ18 f *= 1 - lambda (1 - P/Pbar) (Eq. 18).  Per-view, a cell met by
+ * several rays of the view takes the weighted (by coefficient) geometric mean
+ * of their ratios (POWER) or arithmetic mean of their Eq. 18 factors. */
 enum { USPG_POWER = 0, USPG_LINEAR_EQ18 = 1 };
 /* resample modes (Sec. II.B) */
 enum { USPG_RESAMPLE_POINT = 0, USPG_RESAMPLE_BIJECTION = 1 };
@@ -130,10 +133,10 @@ typedef struct {
 typedef struct {
     int32_t iterations;
     int32_t schedule;    /* USPG_SEQUENTIAL | USPG_PER_VIEW */
-    int32_t update_rule; /* USPG_POWER | USPG_LINEAR_EQ18 (sequential only) */
+    int32_t update_rule; /* USPG_POWER | USPG_LINEAR_EQ18 */
     int32_t view_steps;  /* PER_VIEW: stop after this many view steps (0 = all) */
     double lambda;             /* relaxation (beta of Eq. 18), in (0, 2) */
-    double stop_tol;           /* Eq. 19 tolerance; 0 = run all iterations */
+    double stop_tol;           /* Eq. 19 tolerance; 0 = run all iterations (PER_VIEW: not with view_steps) */
     const int32_t *view_order; /* host, [n_views] permutation for PER_VIEW; NULL = 0..n_views-1 */
 } uspg_mart_opts;
 
@@ -194,7 +197,12 @@ uspg_status uspg_get_row(const uspg_ctx *ctx, int32_t view, int32_t ray, int32_t
 
 /* Projections P_{p,l} of Eq. 17, float32 [views][rays], copied into the
  * context (host source: staged with cudaMemcpyAsync, so the call may return
- * before the copy ends only for page-locked memory). */
+ * before the copy ends only for page-locked memory).  Every value must be a
+ * finite number >= 0 (measured line integrals; noisy data clamped at 0).  Host
+ * data are checked before anything is copied: EINVAL names the first bad
+ * value.  Device data are checked while they are copied: a bad value raises
+ * the context's device flag, which the next uspg_sync reports as EDEVICE.  A
+ * ray whose value is bad is skipped by every schedule (it changes no cell). */
 uspg_status uspg_set_projections(uspg_ctx *ctx, const float *p, int32_t on_device, uspg_stream stream);
 /* Image f_v, float32 [cells]. */
 uspg_status uspg_set_image(uspg_ctx *ctx, const float *f, int32_t on_device, uspg_stream stream);
@@ -209,10 +217,14 @@ uspg_status uspg_get_image(const uspg_ctx *ctx, float *f, int32_t to_device, usp
  * SEQUENTIAL: views 0..p-1 in order, rays in order, each ray's cells corrected
  *   before the next ray (one persistent kernel).
  * PER_VIEW: for each view of view_order, all ray sums with the current image,
- *   then each cell corrected once by the weighted geometric mean of its rays'
- *   ratios (P = 0 rays zero their cells).
- * With stop_tol > 0 (SEQUENTIAL), stops after the first sweep in which every
- * correction satisfies Eq. 19.  ENOTREADY without coefficients or projections.
+ *   then each cell corrected once from all of the view's rays that meet it:
+ *   POWER, the weighted geometric mean of their ratios P/Pbar (P = 0 rays zero
+ *   their cells); LINEAR_EQ18, the weighted arithmetic mean of their Eq. 18
+ *   factors 1 - lambda (1 - P/Pbar).
+ * With stop_tol > 0, stops after the first sweep in which every correction
+ * satisfies Eq. 19, |f_new - f_old| <= stop_tol |f_old| (PER_VIEW: checked on
+ * the device after each sweep, the remaining view steps do nothing; EINVAL
+ * together with view_steps).  ENOTREADY without coefficients or projections.
  * A segment-store context serves SEQUENTIAL only (EUNSUPPORTED for PER_VIEW;
  * likewise uspg_forward_project, uspg_autotune, uspg_mart_kernel_times,
  * batches and server jobs, which read the representative store). */
@@ -220,8 +232,8 @@ uspg_status uspg_mart(uspg_ctx *ctx, const uspg_mart_opts *opts, uspg_stream str
 /* Forward projection of one view with the current image (Eq. 17):
  * out = device float32 [rays]. */
 uspg_status uspg_forward_project(uspg_ctx *ctx, int32_t view, float *out, uspg_stream stream);
-/* Sweeps run by the last uspg_mart (SEQUENTIAL with stop_tol > 0: may be
- * fewer than requested).  Synchronous. */
+/* Sweeps run by the last uspg_mart (with stop_tol > 0: may be fewer than
+ * requested).  Synchronous. */
 uspg_status uspg_mart_sweeps(uspg_ctx *ctx, int32_t *sweeps);
 
 /* --- batched reconstructions ---------------------------------------------------- */
@@ -239,8 +251,9 @@ typedef struct uspg_batch uspg_batch;
  * Creation tunes the blocks-per-work ratio on the first steps (images are
  * saved and restored) and captures the graph.  The contexts must stay alive,
  * and must not rebuild their coefficients, until uspg_batch_destroy.
- * Synchronous.  opts->view_order, view_steps and stop_tol are ignored;
- * errors are reported through uspg_last_error(NULL). */
+ * Synchronous.  opts->view_order, view_steps and stop_tol are ignored; the
+ * batch applies the POWER rule (EUNSUPPORTED for another); errors are
+ * reported through uspg_last_error(NULL). */
 uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_opts *opts, uspg_stream stream,
                               uspg_batch **out);
 /* One batched run (one graph launch) on `stream`. */
@@ -284,8 +297,7 @@ typedef struct {
     uspg_grid_desc grid;      /* grid.sectors (CUSTOM) is copied at submit */
     uspg_scan_desc scan;
     uspg_coeff_opts coeff;
-    uspg_mart_opts mart;      /* view_order, view_steps and stop_tol are ignored for PER_VIEW;
-                                 PER_VIEW takes the POWER rule */
+    uspg_mart_opts mart;      /* view_order, view_steps and stop_tol are ignored for PER_VIEW */
     const float *projections; /* host float32 [views][rays]: copied at submit, or read in place
                                  with USPG_JOB_BORROW_PROJECTIONS */
     float f0;                 /* initial value of every cell */
@@ -322,7 +334,7 @@ typedef struct {
 uspg_status uspg_server_create(size_t device_budget, int32_t max_active, int32_t chunk_sweeps, uspg_server **out);
 /* Copies the job (projections included) into the queue and returns its id.
  * EINVAL for a malformed job (NULL projections, iterations < 1, lambda
- * outside (0, 2), bad sizes); EUNSUPPORTED for PER_VIEW with LINEAR_EQ18.
+ * outside (0, 2), an unknown rule, bad sizes).
  * Geometry errors surface later as the job's status. */
 uspg_status uspg_server_submit(uspg_server *server, const uspg_job *job, uint64_t *id);
 /* ENOTREADY while job `id` is queued or running.  Once it has ended: fills
@@ -353,8 +365,8 @@ uspg_status uspg_resample_cartesian(uspg_ctx *ctx, int32_t mode, int32_t nx, int
 /* Capacity, in rays, of the accumulator used by uspg_forward_project_noalloc. */
 #define USPG_NOALLOC_MAX_RAYS (1 << 20)
 
-/* Forward projection of one view, out = A_view f (the ray sums of Eq. 17),
- * for callers that must not allocate device memory while they run: processes
+/* Forward projection of one view, out = A_view f (the ray sums of view
+ * `view` for the image f), for callers that must not allocate device memory while they run: processes
  * whose device memory is owned by a pooling allocator with a fixed budget
  * (an allocation outside the pool can fail or fragment memory the pool
  * expects to own), and latency-critical loops that forbid cudaMalloc after

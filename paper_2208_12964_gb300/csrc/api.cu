@@ -2,6 +2,7 @@
 // (Eq. 1-2), view classes (Sec. III.C), device buffers, data movement, the
 // MART driver and its CUDA-graph cache.
 #include "internal.cuh"
+#include "device.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -99,8 +100,8 @@ static uspg_status alloc_state(uspg_ctx *c)
     USPG_CUDA(c, cudaMemset(c->d_sacc, 0, sizeof(float) * c->n_rays));
     USPG_CUDA(c, cudaMalloc(&c->d_status, sizeof(int)));
     USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
-    USPG_CUDA(c, cudaMalloc(&c->d_sweeps, sizeof(int)));
-    USPG_CUDA(c, cudaMemset(c->d_sweeps, 0, sizeof(int)));
+    USPG_CUDA(c, cudaMalloc(&c->d_sweeps, sizeof(int) * 4));
+    USPG_CUDA(c, cudaMemset(c->d_sweeps, 0, sizeof(int) * 4));
     USPG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     return USPG_OK;
 }
@@ -402,6 +403,7 @@ uspg_status uspg_sync(uspg_ctx *c, uspg_stream stream)
         if (st & kStatusCountMismatch) os << "row count changed between generator passes; ";
         if (st & kStatusRing0Overflow) os << "too many crossings in the innermost ring; ";
         if (st & kStatusBounds) os << "index out of range; ";
+        if (st & kStatusBadData) os << "device projections hold a value that is not finite and >= 0; ";
         return fail(c, USPG_EDEVICE, os.str());
     }
     return USPG_OK;
@@ -548,14 +550,59 @@ uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t 
     return USPG_OK;
 }
 
+// index of the first value that is not a finite number >= 0, or -1 (IEEE
+// bit patterns: +0 .. the largest finite float, or -0)
+static long long first_bad_value(const float *p, size_t n)
+{
+    const uint32_t *u = (const uint32_t *)p;
+    const size_t chunk = 4096;
+    for (size_t b = 0; b < n; b += chunk) {
+        size_t e = std::min(n, b + chunk);
+        uint32_t bad = 0;
+        for (size_t i = b; i < e; i++) bad |= (uint32_t)(u[i] >= 0x7f800000u) & (uint32_t)(u[i] != 0x80000000u);
+        if (bad)
+            for (size_t i = b; i < e; i++)
+                if (u[i] >= 0x7f800000u && u[i] != 0x80000000u) return (long long)i;
+    }
+    return -1;
+}
+
+// device copy of projections that flags any value that is not finite and >= 0
+__global__ void k_copy_checked(const float *__restrict__ src, float *__restrict__ dst, long long n, int *status)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (i < n) {
+        float v = src[i];
+        dst[i] = v;
+        bad = !(v >= 0.0f && v <= 3.402823466e38f);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusBadData);
+}
+
 uspg_status uspg_set_projections(uspg_ctx *c, const float *p, int32_t on_device, uspg_stream stream)
 {
     if (!c || !p) return fail(c, USPG_EINVAL, "NULL argument");
+    size_t n = (size_t)c->scan.n_views * c->n_rays;
+    if (!on_device) {  // host data are checked here, before anything is copied
+        long long bad = first_bad_value(p, n);
+        if (bad >= 0) {
+            std::ostringstream os;
+            os << "projection " << bad << " (view " << bad / c->n_rays << ", ray " << bad % c->n_rays
+               << ") is " << p[bad] << ": projections must be finite and >= 0";
+            return fail(c, USPG_EINVAL, os.str());
+        }
+    }
     uspg_status st = ensure_state(c);
     if (st) return st;
-    size_t bytes = sizeof(float) * (size_t)c->scan.n_views * c->n_rays;
-    USPG_CUDA(c, cudaMemcpyAsync(c->d_proj, p, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                 (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (on_device) {  // checked while copied; a bad value is reported by uspg_sync (EDEVICE)
+        k_copy_checked<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, c->d_proj, (long long)n, c->d_status);
+        launch_counter()++;
+        USPG_CUDA(c, cudaGetLastError());
+    } else {
+        USPG_CUDA(c, cudaMemcpyAsync(c->d_proj, p, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    }
     c->have_proj = true;
     return USPG_OK;
 }
@@ -642,8 +689,13 @@ static uspg_status per_view(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s
     }
     long long steps = (long long)o->iterations * nv;
     if (o->view_steps > 0 && o->view_steps < steps) steps = o->view_steps;
+    const int linear = o->update_rule == USPG_LINEAR_EQ18;
+    const bool stop = o->stop_tol > 0.0;
+    int *stop_flags = c->d_sweeps;  // [0] sweeps run, [1] a cell moved, [2] converged
+    UpdateRule U{(float)o->lambda, linear, stop ? (float)o->stop_tol : 0.0f, stop_flags + 1};
+    const int *done = stop ? stop_flags + 2 : nullptr;
     std::ostringstream key;
-    key << steps << ':' << o->lambda;
+    key << steps << ':' << o->lambda << ':' << linear << ':' << o->stop_tol;
     for (int k : order) key << ',' << k;
     auto it = c->graphs.find(key.str());
     if (it == c->graphs.end()) {
@@ -651,11 +703,12 @@ static uspg_status per_view(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s
         cudaStream_t cs = c->cap_stream;
         int64_t before = launch_counter();
         USPG_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        uspg_status st = USPG_OK;
+        uspg_status st = stop ? launch_stop_reset(c, cs) : USPG_OK;
         for (long long q = 0; q < steps && !st; q++) {
             int k = order[q % nv];
-            st = launch_forward_view(c, k, nullptr, c->d_res, cs);
-            if (!st) st = launch_backward_view(c, k, (float)o->lambda, cs);
+            st = launch_forward_view(c, k, nullptr, c->d_res, cs, linear, done);
+            if (!st) st = launch_backward_view(c, k, U, done, cs);
+            if (!st && stop && q % nv == nv - 1) st = launch_sweep_end(c, cs);  // Eq. 19 after each sweep
         }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -695,9 +748,12 @@ uspg_status uspg_mart(uspg_ctx *c, const uspg_mart_opts *o, uspg_stream stream)
     if (o->schedule != USPG_PER_VIEW) return fail(c, USPG_EINVAL, "unknown schedule");
     if (c->store_form == USPG_STORE_SEGMENTS)
         return fail(c, USPG_EUNSUPPORTED, "the segment store serves the ray-sequential schedule");
-    if (o->update_rule != USPG_POWER)
-        return fail(c, USPG_EUNSUPPORTED, "the per-view schedule uses the power (geometric-mean) update");
-    if (o->stop_tol != 0.0) return fail(c, USPG_EUNSUPPORTED, "stop_tol applies to the sequential schedule");
+    if (o->update_rule != USPG_POWER && o->update_rule != USPG_LINEAR_EQ18)
+        return fail(c, USPG_EINVAL, "unknown update rule");
+    if (o->stop_tol < 0.0) return fail(c, USPG_EINVAL, "stop_tol must be >= 0");
+    if (o->stop_tol > 0.0 && o->view_steps > 0)
+        return fail(c, USPG_EINVAL, "stop_tol (Eq. 19, checked after whole sweeps) excludes view_steps");
+    if (o->stop_tol > 0.0) c->last_sweeps = -1;  // the sweeps run are read back from the device
     return per_view(c, o, s);
 }
 
@@ -710,6 +766,10 @@ uspg_status uspg_mart_kernel_times(uspg_ctx *c, const uspg_mart_opts *o, float *
     if (o->schedule != USPG_PER_VIEW) return fail(c, USPG_EINVAL, "kernel timing covers the per-view schedule");
     if (c->store_form == USPG_STORE_SEGMENTS)
         return fail(c, USPG_EUNSUPPORTED, "the segment store serves the ray-sequential schedule");
+    if (o->update_rule != USPG_POWER && o->update_rule != USPG_LINEAR_EQ18)
+        return fail(c, USPG_EINVAL, "unknown update rule");
+    const int linear = o->update_rule == USPG_LINEAR_EQ18;
+    UpdateRule U{(float)o->lambda, linear, 0.0f, nullptr};
     int nv = c->scan.n_views;
     long long steps = (long long)o->iterations * nv;
     if (steps > cap) return fail(c, USPG_EINVAL, "cap < iterations * n_views");
@@ -723,9 +783,9 @@ uspg_status uspg_mart_kernel_times(uspg_ctx *c, const uspg_mart_opts *o, float *
     uspg_status st = USPG_OK;
     for (int it = 0; it < o->iterations && !st; it++)
         for (int v = 0; v < nv && !st; v++, q++) {
-            st = launch_forward_view(c, order[v], nullptr, c->d_res, s);
+            st = launch_forward_view(c, order[v], nullptr, c->d_res, s, linear);
             if (!st) st = (uspg_status)(cudaEventRecord(ev[2 * q + 1], s) ? USPG_ECUDA : USPG_OK);
-            if (!st) st = launch_backward_view(c, order[v], (float)o->lambda, s);
+            if (!st) st = launch_backward_view(c, order[v], U, nullptr, s);
             if (!st) st = (uspg_status)(cudaEventRecord(ev[2 * q + 2], s) ? USPG_ECUDA : USPG_OK);
         }
     cudaError_t e = cudaStreamSynchronize(s);
@@ -760,7 +820,7 @@ uspg_status uspg_autotune(uspg_ctx *c, int32_t *choice, uspg_stream stream)
         for (int rep = 0; rep < 4; rep++) {
             cudaEventRecord(e0, s);
             uspg_status st = fwd ? launch_forward_view(c, 0, nullptr, c->d_res, s)
-                                 : launch_backward_view(c, 0, 1e-3f, s);
+                                 : launch_backward_view(c, 0, UpdateRule{1e-3f, 0, 0.0f, nullptr}, nullptr, s);
             cudaEventRecord(e1, s);
             if (st != USPG_OK || cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
             float ms = 0.f;

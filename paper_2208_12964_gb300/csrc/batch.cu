@@ -69,9 +69,10 @@ __global__ void k_batch_finalize(const BatchInst *__restrict__ inst, long long s
     if (ray >= I.mir.n_rows) return;  // the stored rays (all rays when not mirrored)
     int view = (int)(step % I.n_views);
     if (I.mir.on)
-        finalize_pair(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.mir, I.w_scale, nullptr, (float2 *)I.res);
+        finalize_pair(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.mir, I.w_scale, 0, nullptr,
+                      (float2 *)I.res);
     else
-        finalize_ray(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.w_scale, nullptr, I.res);
+        finalize_ray(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.w_scale, 0, nullptr, I.res);
 }
 
 template <typename WT>
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(256, kBwdMinBlocksMirror) k_batch_backward(con
 {
     const BatchInst &I = inst[blockIdx.y];
     if (step >= I.steps || (int)blockIdx.x >= I.bwd_blocks) return;
+    const UpdateRule U{lambda, 0, 0.0f, nullptr};
     int view = (int)(step % I.n_views);
     int rep = I.view_rep[view];
     long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -87,11 +89,11 @@ __global__ void __launch_bounds__(256, kBwdMinBlocksMirror) k_batch_backward(con
     if (I.mir.on)  // block-uniform
         bwd_slices<WT, true>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
                              I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt,
-                             I.view_mg[view], I.cps, I.S, lambda, wg, W, threadIdx.x & 31, I.mir);
+                             I.view_mg[view], I.cps, I.S, U, wg, W, threadIdx.x & 31, I.mir);
     else
         bwd_slices<WT, false>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
                               I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt,
-                              I.view_mg[view], I.cps, I.S, lambda, wg, W, threadIdx.x & 31, I.mir);
+                              I.view_mg[view], I.cps, I.S, U, wg, W, threadIdx.x & 31, I.mir);
 }
 
 }  // namespace uspg

@@ -199,27 +199,47 @@ __device__ __forceinline__ void fwd_groups(const uint32_t *__restrict__ idx, con
     }
 }
 
-__device__ __forceinline__ float log_ratio(float sv, float p)
+// Per-view update rule of the correction kernels (Sec. III.D):
+//  power (linear == 0): f *= exp(lambda * sum w ln(P/Pbar) / sum w), the
+//      weighted geometric mean of the view's ray ratios;
+//  Eq. 18 (linear == 1): f *= sum w (1 - lambda (1 - P/Pbar)) / sum w, the
+//      weighted arithmetic mean of the rays' Eq. 18 factors.
+// tol > 0 (Eq. 19): every cell whose correction moves it by more than
+// tol * |f_old| sets *moved.
+struct UpdateRule {
+    float lambda;
+    int linear;
+    float tol;
+    int *moved;
+};
+
+// The ray value the correction averages: ln(P/Pbar) (power rule; -inf for
+// P = 0, which zeroes the cells of the ray) or P/Pbar (Eq. 18).  NaN marks a
+// ray to skip: empty row or zero sum, or a projection that is not a finite
+// non-negative number (such data are refused at input; a ray that carries
+// one anyway changes nothing).
+__device__ __forceinline__ float ray_value(float sv, float p, int linear)
 {
-    // NaN marks a ray to skip (empty row or zero sum), -inf a ray with P = 0
-    if (!(sv > 0.0f)) return __int_as_float(0x7fc00000);
+    if (!(sv > 0.0f) || !(p >= 0.0f && p <= 3.402823466e38f)) return __int_as_float(0x7fc00000);
+    if (linear) return p / sv;
     return p > 0.0f ? logf(p / sv) : -INFINITY;
 }
 
-// ln(P/Pbar) of one ray from its accumulated sum; clears the accumulator.
+// Ray value of one ray from its accumulated sum; clears the accumulator.
 __device__ __forceinline__ void finalize_ray(float *__restrict__ sacc, const float *__restrict__ proj, int ray,
-                                             float w_scale, float *__restrict__ out_s, float *__restrict__ out_res)
+                                             float w_scale, int linear, float *__restrict__ out_s,
+                                             float *__restrict__ out_res)
 {
     float sv = sacc[ray] * w_scale;
     sacc[ray] = 0.0f;
     if (out_s) out_s[ray] = sv;
-    if (out_res) out_res[ray] = log_ratio(sv, proj[ray]);
+    if (out_res) out_res[ray] = ray_value(sv, proj[ray], linear);
 }
 
-// z-mirror store: stored ray r and its mirror; out_res2[r] = {ln ratio of r,
-// ln ratio of mirror(r)} (the pair the correction gathers in one load).
+// z-mirror store: stored ray r and its mirror; out_res2[r] = {value of r,
+// value of mirror(r)} (the pair the correction gathers in one load).
 __device__ __forceinline__ void finalize_pair(float *__restrict__ sacc, const float *__restrict__ proj, int ray,
-                                              const Mirror &M, float w_scale, float *__restrict__ out_s,
+                                              const Mirror &M, float w_scale, int linear, float *__restrict__ out_s,
                                               float2 *__restrict__ out_res2)
 {
     int rm = mirror_ray(ray, M.n_u, M.n_v);
@@ -231,7 +251,8 @@ __device__ __forceinline__ void finalize_pair(float *__restrict__ sacc, const fl
         out_s[ray] = sv;
         out_s[rm] = sm;
     }
-    if (out_res2) out_res2[ray] = make_float2(log_ratio(sv, proj[ray]), log_ratio(sm, proj[rm]));
+    if (out_res2)
+        out_res2[ray] = make_float2(ray_value(sv, proj[ray], linear), ray_value(sm, proj[rm], linear));
 }
 
 struct SliceDesc {
@@ -253,8 +274,8 @@ __device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_o
     }
 }
 
-// One present entry (weight wt > 0) of a cell: a ray with log-ratio NaN is
-// skipped; -inf (P = 0) zeroes the cell, whatever num becomes.
+// One present entry (weight wt > 0) of a cell: a ray with value NaN is
+// skipped; -inf (power rule, P = 0) zeroes the cell, whatever num becomes.
 __device__ __forceinline__ void acc_entry(float wt, float r, float &num, float &den, bool &zero)
 {
     if (wt > 0.0f && r == r) {
@@ -264,13 +285,22 @@ __device__ __forceinline__ void acc_entry(float wt, float r, float &num, float &
     }
 }
 
-// f * exp(lambda * num / den) of a cell hit by at least one ray (den > 0),
-// 0 if one of its rays has P = 0.  The ratio is a weighted mean of
-// log-ratios, so the fast reciprocal and exponential (a few units in the
-// last place) are far inside the image tolerance.
-__device__ __forceinline__ float cell_update(float fv, float num, float den, bool zero, float lambda)
+// New value of a cell met by at least one ray (den > 0).  Power rule:
+// f * exp(lambda * num / den), 0 if one of its rays has P = 0; Eq. 18:
+// f * (1 - lambda + lambda * num / den).  The ratio is a weighted mean, so
+// the fast reciprocal and exponential (a few units in the last place) are far
+// inside the image tolerance.
+__device__ __forceinline__ float cell_update(float fv, float num, float den, bool zero, const UpdateRule &U)
 {
-    return zero ? 0.0f : fv * __expf(lambda * __fdividef(num, den));
+    float m = __fdividef(num, den);
+    if (U.linear) return fv * fmaf(U.lambda, m, 1.0f - U.lambda);
+    return zero ? 0.0f : fv * __expf(U.lambda * m);
+}
+
+// Eq. 19: does the correction fv -> nv break |nv - fv| <= tol |fv|?
+__device__ __forceinline__ bool moved_cell(float fv, float nv, const UpdateRule &U)
+{
+    return U.tol > 0.0f && fabsf(nv - fv) > U.tol * fabsf(fv);
 }
 
 // Per-lane correction sums of one cell (and, MIR, of its mirror cell).
@@ -333,8 +363,8 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
                                            const uint16_t *__restrict__ lane_desc, const uint32_t *__restrict__ cray,
                                            const WT *__restrict__ cw, const float *__restrict__ res,
                                            float *__restrict__ f, const RingEntry *__restrict__ rt, int mG,
-                                           long long cps, long long n_slices, float lambda, long long wg, long long W,
-                                           int lane, const Mirror &M)
+                                           long long cps, long long n_slices, const UpdateRule &U, long long wg,
+                                           long long W, int lane, const Mirror &M)
 {
     long long sl = wg;
     if (sl >= n_slices) return;
@@ -384,13 +414,18 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
                 }
             }
         }
+        bool mv = false;
         if (MIR) {
-            float nx = S.den > 0.0f ? cell_update(fv, S.num, S.den, S.zero, lambda) : fv;
-            float ny = !pair ? nx : (S.denm > 0.0f ? cell_update(fm, S.numm, S.denm, S.zerom, lambda) : fm);
+            float nx = S.den > 0.0f ? cell_update(fv, S.num, S.den, S.zero, U) : fv;
+            float ny = !pair ? nx : (S.denm > 0.0f ? cell_update(fm, S.numm, S.denm, S.zerom, U) : fm);
             if (S.den > 0.0f || (pair && S.denm > 0.0f)) ((float2 *)f)[k] = make_float2(nx, ny);
+            mv = moved_cell(fv, nx, U) || moved_cell(fm, ny, U);
         } else if (S.den > 0.0f) {
-            *fp = cell_update(fv, S.num, S.den, S.zero, lambda);
+            float nv = cell_update(fv, S.num, S.den, S.zero, U);
+            *fp = nv;
+            mv = moved_cell(fv, nv, U);
         }
+        if (U.tol > 0.0f && __any_sync(0xffffffffu, mv) && lane == 0) *U.moved = 1;
         cur = nxt;
     }
 }

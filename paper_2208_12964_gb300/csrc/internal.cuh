@@ -33,6 +33,7 @@ constexpr int kStatusRing0Overflow = 2;
 constexpr int kStatusBounds = 4;
 constexpr int kStatusTimeout = 8;
 constexpr int kStatusCellRays = 16;
+constexpr int kStatusBadData = 32;  // device projections with a value that is not finite and >= 0
 constexpr int kMaxCellRays = 2047;  // rays of one view through one cell (11-bit lane count)
 
 // Stored cell index of a representative row: slab (10 b) | ring (10 b) | sector (12 b).
@@ -191,7 +192,7 @@ struct uspg_ctx {
     bool have_proj = false;
     float *d_res = nullptr;  // per-ray log-ratio scratch [n_rays]
     int *d_status = nullptr;
-    int *d_sweeps = nullptr;
+    int *d_sweeps = nullptr;  // [4]: sweeps run, and the per-view Eq. 19 flags (moved, converged)
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, uspg::Graph> graphs;
     int last_sweeps = 0;
@@ -224,8 +225,15 @@ uspg_status launch_sequential_segments(uspg_ctx *c, const uspg_mart_opts *o, cud
 uspg_status segment_row(uspg_ctx *c, int view, int ray, std::vector<long long> &cells);
 void free_segments(uspg_ctx *c);
 // mart.cu
-uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s);
-uspg_status launch_backward_view(uspg_ctx *c, int view, float lambda, cudaStream_t s);
+struct UpdateRule;
+// linear = 1: the ray values are P/Pbar (Eq. 18) instead of ln(P/Pbar); done
+// (device, may be NULL): the per-view kernels do nothing once *done != 0
+uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s, int linear = 0,
+                                const int *done = nullptr);
+uspg_status launch_backward_view(uspg_ctx *c, int view, const UpdateRule &U, const int *done, cudaStream_t s);
+// Eq. 19 bookkeeping of a per-view run on c->d_sweeps[0..2] (sweeps, moved, converged)
+uspg_status launch_stop_reset(uspg_ctx *c, cudaStream_t s);
+uspg_status launch_sweep_end(uspg_ctx *c, cudaStream_t s);
 uspg_status launch_sequential(uspg_ctx *c, const uspg_mart_opts *o, cudaStream_t s);
 // device bytes currently held by a context (its own buffers only)
 long long ctx_device_bytes(const uspg_ctx *c);

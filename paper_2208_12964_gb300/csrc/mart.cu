@@ -54,31 +54,60 @@ __global__ void __launch_bounds__(256) k_forward_flat(const uint32_t *__restrict
                                                       const uint32_t *__restrict__ grp_ray, long long g0,
                                                       long long n_groups, const float *__restrict__ f,
                                                       const RingEntry *__restrict__ rt, int n_rings, int mG,
-                                                      long long cps, float *__restrict__ sacc, Mirror M)
+                                                      long long cps, float *__restrict__ sacc, Mirror M,
+                                                      const int *__restrict__ done)
 {
     extern __shared__ int4 tab[];
     fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
     __syncthreads();
+    if (done) {  // Eq. 19 stop: nothing to do once the iteration has converged
+        grid_dep_wait();
+        if (*done) return;
+    }
     fwd_groups<WT, MIR, PAIRS>(idx, w, grp_ray, g0, n_groups, f, tab, cps, sacc,
                                ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                                ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
 }
 
 __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__restrict__ proj, int n_rays, float w_scale,
-                                   float *__restrict__ out_s, float *__restrict__ out_res)
+                                   int linear, float *__restrict__ out_s, float *__restrict__ out_res,
+                                   const int *__restrict__ done)
 {
     grid_dep_wait();
+    if (done && *done) return;
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray < n_rays) finalize_ray(sacc, proj, ray, w_scale, out_s, out_res);
+    if (ray < n_rays) finalize_ray(sacc, proj, ray, w_scale, linear, out_s, out_res);
 }
 
 // z-mirror store: one thread per stored ray finalizes it and its mirror
 __global__ void k_forward_finalize_pairs(float *__restrict__ sacc, const float *__restrict__ proj, Mirror M,
-                                         float w_scale, float *__restrict__ out_s, float *__restrict__ out_res)
+                                         float w_scale, int linear, float *__restrict__ out_s,
+                                         float *__restrict__ out_res, const int *__restrict__ done)
 {
     grid_dep_wait();
+    if (done && *done) return;
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray < M.n_rows) finalize_pair(sacc, proj, ray, M, w_scale, out_s, (float2 *)out_res);
+    if (ray < M.n_rows) finalize_pair(sacc, proj, ray, M, w_scale, linear, out_s, (float2 *)out_res);
+}
+
+// Eq. 19 bookkeeping of a per-view run that may stop early (stop[0] = sweeps
+// run, stop[1] = some correction of the current sweep moved a cell by more
+// than the tolerance, stop[2] = converged): reset before the first sweep, and
+// after each sweep count it and stop if no cell moved.
+__global__ void k_stop_reset(int *stop)
+{
+    stop[0] = 0;
+    stop[1] = 0;
+    stop[2] = 0;
+}
+
+__global__ void k_sweep_end(int *stop)
+{
+    grid_dep_wait();
+    if (stop[2]) return;
+    stop[0]++;
+    if (!stop[1]) stop[2] = 1;
+    stop[1] = 0;
 }
 
 // ---- per-view correction: lane-ordered cell-major store --------------------------
@@ -95,10 +124,14 @@ __global__ void __launch_bounds__(256, MIR ? kBwdMinBlocksMirror : kBwdMinBlocks
     k_backward_sell(const long long *__restrict__ slice_off, long long base, const uint32_t *__restrict__ slice_meta,
                     const uint16_t *__restrict__ lane_desc, const uint32_t *__restrict__ cray,
                     const WT *__restrict__ cw, const float *__restrict__ res, float *__restrict__ f,
-                    const RingEntry *__restrict__ rt, int mG, long long cps, long long n_slices, float lambda,
-                    Mirror M)
+                    const RingEntry *__restrict__ rt, int mG, long long cps, long long n_slices, UpdateRule U,
+                    Mirror M, const int *__restrict__ done)
 {
-    bwd_slices<WT, MIR>(slice_off, base, slice_meta, lane_desc, cray, cw, res, f, rt, mG, cps, n_slices, lambda,
+    if (done) {
+        grid_dep_wait();
+        if (*done) return;
+    }
+    bwd_slices<WT, MIR>(slice_off, base, slice_meta, lane_desc, cray, cw, res, f, rt, mG, cps, n_slices, U,
                         ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                         ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
 }
@@ -135,7 +168,8 @@ static int sm_count()
 // for a caller's standard-layout image
 template <typename WT>
 static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, bool f_pairs, float *acc, float *out_s,
-                           float *out_res, const float *proj, cudaStream_t s)
+                           float *out_res, const float *proj, cudaStream_t s, int linear = 0,
+                           const int *done = nullptr)
 {
     int rep = c->rep_of_view[view];
     int mG = c->m_of_view[view] % c->G;
@@ -153,38 +187,40 @@ static uspg_status fwd_run(uspg_ctx *c, int view, const float *f, bool f_pairs, 
     cudaError_t e;
     if (c->mir.on && f_pairs)
         e = launch_pdl(k_forward_flat<WT, true, true>, (unsigned)grid, TB, smem, s, idx, w, grp, g0, ng, f, rt,
-                       c->n_rings, mG, cps, acc, c->mir);
+                       c->n_rings, mG, cps, acc, c->mir, done);
     else if (c->mir.on)
         e = launch_pdl(k_forward_flat<WT, true, false>, (unsigned)grid, TB, smem, s, idx, w, grp, g0, ng, f, rt,
-                       c->n_rings, mG, cps, acc, c->mir);
+                       c->n_rings, mG, cps, acc, c->mir, done);
     else
         e = launch_pdl(k_forward_flat<WT, false, false>, (unsigned)grid, TB, smem, s, idx, w, grp, g0, ng, f, rt,
-                       c->n_rings, mG, cps, acc, c->mir);
+                       c->n_rings, mG, cps, acc, c->mir, done);
     launch_counter()++;
     USPG_CUDA(c, e);
     float ws = (float)c->w_scale;
     if (c->mir.on)
         e = launch_pdl(k_forward_finalize_pairs, (unsigned)((c->mir.n_rows + 255) / 256), 256, 0, s, acc, proj,
-                       c->mir, ws, out_s, out_res);
+                       c->mir, ws, linear, out_s, out_res, done);
     else
         e = launch_pdl(k_forward_finalize, (unsigned)((c->n_rays + 255) / 256), 256, 0, s, acc, proj, c->n_rays, ws,
-                       out_s, out_res);
+                       linear, out_s, out_res, done);
     launch_counter()++;
     USPG_CUDA(c, e);
     return USPG_OK;
 }
 
-uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s)
+uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s, int linear,
+                                const int *done)
 {
     const float *proj = c->d_proj + (long long)view * c->n_rays;
-    if (c->dtype == USPG_F16) return fwd_run<__half>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s);
+    if (c->dtype == USPG_F16)
+        return fwd_run<__half>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s, linear, done);
     if (c->dtype == USPG_BF16)
-        return fwd_run<__nv_bfloat16>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s);
-    return fwd_run<float>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s);
+        return fwd_run<__nv_bfloat16>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s, linear, done);
+    return fwd_run<float>(c, view, c->d_f, true, c->d_sacc, out_s, out_res, proj, s, linear, done);
 }
 
 template <typename WT>
-static uspg_status bwd_typed(uspg_ctx *c, int view, float lambda, cudaStream_t s)
+static uspg_status bwd_typed(uspg_ctx *c, int view, const UpdateRule &U, const int *done, cudaStream_t s)
 {
     int rep = c->rep_of_view[view];
     int mG = c->m_of_view[view] % c->G;
@@ -204,21 +240,37 @@ static uspg_status bwd_typed(uspg_ctx *c, int view, float lambda, cudaStream_t s
     if (c->mir.on)
         e = launch_pdl(k_backward_sell<WT, true>, (unsigned)grid, TB, 0, s, so, base, meta, ld,
                        (const uint32_t *)c->d_cm_ray, cw, res, c->d_f, (const RingEntry *)c->d_ring, mG,
-                       c->cells_per_slab, S, lambda, c->mir);
+                       c->cells_per_slab, S, U, c->mir, done);
     else
         e = launch_pdl(k_backward_sell<WT, false>, (unsigned)grid, TB, 0, s, so, base, meta, ld,
                        (const uint32_t *)c->d_cm_ray, cw, res, c->d_f, (const RingEntry *)c->d_ring, mG,
-                       c->cells_per_slab, S, lambda, c->mir);
+                       c->cells_per_slab, S, U, c->mir, done);
     launch_counter()++;
     USPG_CUDA(c, e);
     return USPG_OK;
 }
 
-uspg_status launch_backward_view(uspg_ctx *c, int view, float lambda, cudaStream_t s)
+uspg_status launch_backward_view(uspg_ctx *c, int view, const UpdateRule &U, const int *done, cudaStream_t s)
 {
-    if (c->dtype == USPG_F16) return bwd_typed<__half>(c, view, lambda, s);
-    if (c->dtype == USPG_BF16) return bwd_typed<__nv_bfloat16>(c, view, lambda, s);
-    return bwd_typed<float>(c, view, lambda, s);
+    if (c->dtype == USPG_F16) return bwd_typed<__half>(c, view, U, done, s);
+    if (c->dtype == USPG_BF16) return bwd_typed<__nv_bfloat16>(c, view, U, done, s);
+    return bwd_typed<float>(c, view, U, done, s);
+}
+
+uspg_status launch_stop_reset(uspg_ctx *c, cudaStream_t s)
+{
+    k_stop_reset<<<1, 1, 0, s>>>(c->d_sweeps);
+    launch_counter()++;
+    USPG_CUDA(c, cudaGetLastError());
+    return USPG_OK;
+}
+
+uspg_status launch_sweep_end(uspg_ctx *c, cudaStream_t s)
+{
+    cudaError_t e = launch_pdl(k_sweep_end, 1, 1, 0, s, c->d_sweeps);
+    launch_counter()++;
+    USPG_CUDA(c, e);
+    return USPG_OK;
 }
 
 // ---- faithful ray-sequential MART -----------------------------------------------
@@ -344,7 +396,7 @@ __global__ void __launch_bounds__(32) k_sequential(const long long *__restrict__
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                     float s = acc * w_scale;
-                    if (s > 0.0f) {
+                    if (s > 0.0f && cp >= 0.0f && cp <= 3.402823466e38f) {  // a bad projection changes nothing
                         float ratio = cp / s;
                         float l2 = log2f(ratio);
                         float ex = lambda / cmx;

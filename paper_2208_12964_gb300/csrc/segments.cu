@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(32) k_seq_seg(const long long *__restrict__ pt
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (acc > 0.0f) {
+                if (acc > 0.0f && p >= 0.0f && p <= 3.402823466e38f) {  // a bad projection changes nothing
                     float ratio = p / acc;
                     float fac = rule == USPG_LINEAR_EQ18 ? 1.0f - lambda * (1.0f - ratio) : powf(ratio, lambda);
                     auto upd = [&](const SegCells &sc) {

@@ -477,8 +477,8 @@ uspg_status uspg_server_submit(uspg_server *s, const uspg_job *job, uint64_t *id
         return uspg::fail(nullptr, USPG_EINVAL, "server: iterations >= 1 and lambda in (0, 2)");
     if (m.schedule != USPG_PER_VIEW && m.schedule != USPG_SEQUENTIAL)
         return uspg::fail(nullptr, USPG_EINVAL, "server: unknown schedule");
-    if (m.schedule == USPG_PER_VIEW && m.update_rule != USPG_POWER)
-        return uspg::fail(nullptr, USPG_EUNSUPPORTED, "server: per-view jobs use the power update");
+    if (m.update_rule != USPG_POWER && m.update_rule != USPG_LINEAR_EQ18)
+        return uspg::fail(nullptr, USPG_EINVAL, "server: unknown update rule");
     if (job->coeff.store_form != USPG_STORE_REPRESENTATIVES)
         return uspg::fail(nullptr, USPG_EUNSUPPORTED, "server: jobs use the representative store");
     int ns = job->scan.geometry == USPG_CONE_3D ? job->scan.n_v : 1;

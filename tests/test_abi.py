@@ -129,3 +129,29 @@ def test_create_validates_fan_scans_and_store_forms(U):
     g5, s5, o5, _ = U.descs_from_spec(seg)
     assert o5.weight_mode == U.BINARY and o5.store_form == U.STORE_SEGMENTS
     U.uspg_destroy(U.uspg_create(g5, s5, o5))
+
+
+@pytest.mark.parametrize("bad", [float("nan"), -0.25, float("inf"), -float("inf")])
+def test_set_projections_refuses_bad_host_data(U, bad):
+    """Projections are measured line integrals: finite and >= 0 (noisy data
+    clamped at 0).  Host data holding anything else are refused with EINVAL
+    before any device work, and the message names the first bad value."""
+    import numpy as np
+
+    from paper_2208_12964_gb300 import synth
+
+    spec = synth.parallel_workload(4, 3, 9)
+    g, s, o, _ = U.descs_from_spec(spec)
+    ctx = U.uspg_create(g, s, o)
+    try:
+        p = np.ones((3, 9), np.float32)
+        p[0, 0] = 0.0
+        p[1, 0] = -0.0  # minus zero is zero
+        p[2, 4] = bad
+        with pytest.raises(U.UspgError) as e:
+            U.uspg_set_projections(ctx, p, False)
+        assert e.value.status == U.EINVAL
+        msg = U.uspg_last_error(ctx)
+        assert "projection 22 (view 2, ray 4)" in msg and "finite and >= 0" in msg
+    finally:
+        U.uspg_destroy(ctx)

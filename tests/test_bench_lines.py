@@ -42,9 +42,12 @@ def test_traffic_record_matches_its_sources_and_geometry():
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic_cone128_mart.json")))
     spec = synth.workload("3d-cone-128r-128s-90v-256")
     t = bench.measured_traffic("k_backward", "f32", True, spec)
-    # the committed capture belongs to the committed kernel sources (a change to
-    # them needs a new capture: until then the line reports null)
-    assert t == rec["kernels"]["128r-128s-256x256/k_backward/f32/mirrored"]["dram_bytes_per_launch"]
+    # a capture belongs to the kernel sources it was taken from: while they are
+    # unchanged the line reports its bytes, after a change null (until a new capture)
+    if bench.sources_hash_matches(rec):
+        assert t == rec["kernels"]["128r-128s-256x256/k_backward/f32/mirrored"]["dram_bytes_per_launch"]
+    else:
+        assert t is None
     # no record for another geometry or store form: the line says null, not a guess
     assert bench.measured_traffic("k_backward", "f32", True, synth.workload("3d-cone-256r-256s-180v-512")) is None
     assert bench.measured_traffic("k_backward", "f16", True, spec) is None

@@ -8,6 +8,7 @@ values, the cell choice is an integer decision taken in FP64 on both sides).
 import numpy as np
 import pytest
 
+import oracle
 from gpu_util import Gpu, assert_rows_equal, oracle_for, rel_l2
 from paper_2208_12964_gb300 import synth
 
@@ -570,3 +571,150 @@ def test_segment_store_sequential_mart(torch_cuda, case, rule):
     with pytest.raises(uspg.UspgError) as e:
         uspg.uspg_mart(g.ctx, uspg.mart_opts(1, 0.4, uspg.PER_VIEW)[0])
     assert e.value.status == uspg.EUNSUPPORTED
+
+
+def test_batched_instances_match_oracle(torch_cuda):
+    """An uneven batch shaped like the 64-instance batched workload (2D
+    parallel instances with 64, 128, 256 and 512 rings, 18 to 90 views, 2R+1
+    bins), plus a mirrored cone (odd detector rows and slab count, Poisson
+    noise) and an off-centre cone (every row stored), advanced together in one
+    graph: every instance's image against the oracle's per-view MART."""
+    import os
+
+    from paper_2208_12964_gb300 import uspg
+
+    specs = [synth.parallel_workload(64, 18, 129, seed=41, iterations=3, lam=0.2),
+             synth.parallel_workload(128, 36, 257, seed=42, iterations=3, lam=0.2),
+             synth.parallel_workload(256, 18, 513, seed=43, iterations=3, lam=0.2),
+             synth.parallel_workload(512, 18, 1025, seed=44, iterations=3, lam=0.2),
+             synth.parallel_workload(64, 90, 129, seed=45, iterations=3, lam=0.2),
+             synth.cone_workload(10, 9, 12, 21, iterations=3, lam=0.2, seed=46),
+             synth.cone_workload(10, 8, 12, 20, iterations=3, lam=0.2, seed=47, noise=False)]
+    specs[-1]["z_min"] = -0.75  # off-centre stack: no z-mirror
+    gs, projs = [], []
+    for sp in specs:
+        g = Gpu(sp).build()
+        p = synth.projections(sp)
+        uspg.uspg_set_projections(g.ctx, p, False)
+        uspg.uspg_fill_image(g.ctx, 1.0)
+        gs.append(g)
+        projs.append(p)
+    assert [g.stats()["mirrored"] for g in gs[-2:]] == [1, 0]
+    opts, _ = uspg.mart_opts(3, 0.2, uspg.PER_VIEW)
+    b = uspg.uspg_batch_create([g.ctx for g in gs], opts)
+    try:
+        uspg.uspg_batch_run(b)
+        torch_cuda.cuda.synchronize()
+    finally:
+        uspg.uspg_batch_destroy(b)
+    for i, (sp, g, p) in enumerate(zip(specs, gs, projs)):
+        n = g.stats()["n_cells"]
+        got = np.zeros(n, np.float32)
+        uspg.uspg_get_image(g.ctx, got, False)
+        o = oracle_for(sp, threads=os.cpu_count() or 8)
+        ref = o.mart_per_view(p, np.ones(n), 3, 0.2)
+        err = rel_l2(got, ref)
+        worst = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        print(f"instance {i} ({sp['name']}): rel-L2 {err:.2e}, max |diff| / max |f| {worst:.2e}")
+        assert err < TOL_IMG, i
+        assert worst < 10 * TOL_IMG, i
+        g.close()
+
+
+@pytest.mark.parametrize("case", ["parallel", "cone_mirror_odd", "cone_off_centre", "cone_f16"])
+def test_mart_per_view_linear_eq18(torch_cuda, case):
+    """Per-view MART with the update of Eq. 18: every cell is corrected once
+    per view by the weighted mean of its rays' factors 1 - beta (1 - P/Pbar),
+    against the oracle (FP32 stores within 1e-4 relative L2; an FP16 store
+    within its rounding)."""
+    from paper_2208_12964_gb300 import uspg
+
+    dtype, tol, beta = uspg.F32, TOL_IMG, 0.2
+    if case == "parallel":
+        spec, beta = synth.parallel_workload(40, 30, 81, seed=7), 0.4
+    elif case == "cone_mirror_odd":
+        spec = synth.cone_workload(10, 9, 12, 21, seed=8)
+    elif case == "cone_off_centre":
+        spec = synth.cone_workload(10, 8, 12, 20, seed=9, noise=False)
+        spec["z_min"] = -0.75
+    else:
+        spec, dtype, tol = synth.cone_workload(16, 12, 24, 32, seed=10), uspg.F16, 2e-3
+    proj = synth.projections(spec)
+    g = Gpu(spec, dtype=dtype).build()
+    o = oracle_for(spec)
+    f0 = np.ones(o.n_cells)
+    ref = o.mart_per_view(proj, f0, 3, beta, rule=oracle.LINEAR_EQ18)
+    got = _run_mart(g, proj, f0, 3, beta, uspg.PER_VIEW, rule=uspg.LINEAR_EQ18)
+    err = rel_l2(got, ref)
+    print(f"{case}: rel-L2 {err:.2e}")
+    assert err < tol
+    assert np.all(got > 0)  # Eq. 18 factors stay positive for beta < 1 and P >= 0
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_mart_per_view_eq19_stop(torch_cuda, rule):
+    """Eq. 19 in the per-view schedule.  Consistent data p = A f* (the
+    oracle's forward projection) started at f*: the first sweep moves no cell
+    by more than 1e-3 of its value, so one sweep runs and the image stays f*.
+    Started at f = 1, with a tolerance chosen where the oracle's decision is
+    robust (the same sweep count for 0.98 and 1.02 times it): the GPU stops
+    after the same sweep as the oracle, with the same image."""
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.parallel_workload(12, 18, 25, seed=5)
+    g = Gpu(spec).build()
+    o = oracle_for(spec)
+    fstar = 0.5 + np.random.default_rng(1).random(o.n_cells)
+    p = np.stack([o.forward(k, fstar) for k in range(18)]).astype(np.float32)
+    got = _run_mart(g, p, fstar, 30, 0.3, uspg.PER_VIEW, rule=rule, tol=1e-3)
+    assert uspg.uspg_mart_sweeps(g.ctx) == 1
+    assert np.max(np.abs(got / fstar - 1)) < 1e-5
+    f0 = np.ones(o.n_cells)
+    pick = None
+    for t in np.logspace(-1, -5, 33):
+        n = [o.mart_per_view(p, f0, 12, 0.3, rule=rule, tol=t * m, return_sweeps=True)[1] for m in (0.98, 1, 1.02)]
+        if n[0] == n[1] == n[2] and 3 <= n[1] < 12:
+            pick = (t, n[1])
+            break
+    assert pick is not None
+    t, n_ref = pick
+    ref = o.mart_per_view(p, f0, 12, 0.3, rule=rule, tol=t)
+    got = _run_mart(g, p, f0, 12, 0.3, uspg.PER_VIEW, rule=rule, tol=t)
+    assert uspg.uspg_mart_sweeps(g.ctx) == n_ref
+    assert rel_l2(got, ref) < TOL_IMG
+    # without a tolerance every sweep runs
+    _run_mart(g, p, f0, 4, 0.3, uspg.PER_VIEW, rule=rule)
+    assert uspg.uspg_mart_sweeps(g.ctx) == 4
+    with pytest.raises(uspg.UspgError) as e:  # Eq. 19 is checked on whole sweeps only
+        uspg.uspg_mart(g.ctx, uspg.mart_opts(2, 0.3, uspg.PER_VIEW, rule, 1e-3, view_steps=5)[0])
+    assert e.value.status == uspg.EINVAL
+
+
+@pytest.mark.parametrize("bad", [float("nan"), -1.0])
+def test_device_projections_with_bad_values_are_flagged(torch_cuda, bad):
+    """Projections handed over in device memory are checked while they are
+    copied: a value that is not finite and >= 0 raises the context's device
+    flag, which uspg_sync reports as EDEVICE (and then clears).  A ray that
+    carries such a value is skipped by both schedules: the image stays finite
+    and non-negative."""
+    torch = torch_cuda
+    from paper_2208_12964_gb300 import uspg
+
+    spec = synth.parallel_workload(12, 18, 25, seed=5)
+    g = Gpu(spec).build()
+    p = torch.from_numpy(synth.projections(spec)).cuda()
+    p[3, 7] = bad
+    uspg.uspg_set_projections(g.ctx, p, True)
+    with pytest.raises(uspg.UspgError) as e:
+        uspg.uspg_sync(g.ctx)
+    assert e.value.status == uspg.EDEVICE
+    assert "finite" in uspg.uspg_last_error(g.ctx)
+    uspg.uspg_sync(g.ctx)  # the flag was cleared when it was reported
+    n = g.stats()["n_cells"]
+    for schedule in (uspg.PER_VIEW, uspg.SEQUENTIAL):
+        uspg.uspg_fill_image(g.ctx, 1.0)
+        uspg.uspg_mart(g.ctx, uspg.mart_opts(2, 0.3, schedule)[0])
+        uspg.uspg_sync(g.ctx)
+        f = np.zeros(n, np.float32)
+        uspg.uspg_get_image(g.ctx, f, False)
+        assert np.all(np.isfinite(f)) and np.all(f >= 0), schedule
