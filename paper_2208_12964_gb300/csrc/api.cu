@@ -94,8 +94,9 @@ static uspg_status alloc_state(uspg_ctx *c)
     if (c->d_f) return USPG_OK;
     USPG_CUDA(c, cudaMalloc(&c->d_f, sizeof(float) * image_floats(c)));
     USPG_CUDA(c, cudaMalloc(&c->d_proj, sizeof(float) * (long long)c->scan.n_views * c->n_rays));
-    // per-ray log-ratios; mirrored stores keep them as pairs per stored ray
-    USPG_CUDA(c, cudaMalloc(&c->d_res, sizeof(float) * std::max<long long>(c->n_rays, 2LL * c->mir.n_rows)));
+    // per-ray correction terms {value, taken part}; mirrored stores keep
+    // them as pairs of terms per stored ray, in both orders (finalize_pair)
+    USPG_CUDA(c, cudaMalloc(&c->d_res, c->mir.on ? sizeof(float4) * 2 * c->mir.n_rows : sizeof(float2) * c->n_rays));
     USPG_CUDA(c, cudaMalloc(&c->d_sacc, sizeof(float) * c->n_rays));
     USPG_CUDA(c, cudaMemset(c->d_sacc, 0, sizeof(float) * c->n_rays));
     USPG_CUDA(c, cudaMalloc(&c->d_status, sizeof(int)));
@@ -216,7 +217,7 @@ long long ctx_device_bytes(const uspg_ctx *c)
 {
     int wb = c->dtype == USPG_F32 ? 4 : 2;
     long long rows = (long long)c->n_reps * c->mir.n_rows, slices = c->slices_per_rep * c->n_reps;
-    long long b = 4LL * c->n_cells + 4LL * c->scan.n_views * c->n_rays + 12LL * c->n_rays;  // image, projections, scratch
+    long long b = 4LL * c->n_cells + 4LL * c->scan.n_views * c->n_rays + 16LL * c->n_rays;  // image, projections, scratch
     if (c->store_src) return b;
     b += (long long)sizeof(RingEntry) * c->n_rings + 24LL * c->cells_per_slab;  // ring table, boundaries
     if (c->d_seg_ptr) b += 20LL * c->n_segments + 9LL * (c->n_rays + 1) + 8LL * c->scan.n_views;

@@ -70,9 +70,9 @@ __global__ void k_batch_finalize(const BatchInst *__restrict__ inst, long long s
     int view = (int)(step % I.n_views);
     if (I.mir.on)
         finalize_pair(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.mir, I.w_scale, 0, nullptr,
-                      (float2 *)I.res);
+                      (float4 *)I.res);
     else
-        finalize_ray(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.w_scale, 0, nullptr, I.res);
+        finalize_ray(I.sacc, I.proj + (long long)view * I.n_rays, ray, I.w_scale, 0, nullptr, (float2 *)I.res);
 }
 
 template <typename WT>

@@ -225,22 +225,35 @@ __device__ __forceinline__ float ray_value(float sv, float p, int linear)
     return p > 0.0f ? logf(p / sv) : -INFINITY;
 }
 
-// Ray value of one ray from its accumulated sum; clears the accumulator.
+// What the correction adds per unit weight for one ray: (value, 1) for a ray
+// that takes part, (0, 0) for a skipped one, so that a cell's sums are plain
+// fused multiply-adds, num += w * x and den += w * y.  A ray with P = 0
+// (power rule) carries -inf and makes num -inf: the cell becomes 0.
+__device__ __forceinline__ float2 ray_term(float sv, float p, int linear)
+{
+    float r = ray_value(sv, p, linear);
+    return r == r ? make_float2(r, 1.0f) : make_float2(0.0f, 0.0f);
+}
+
+// Ray term of one ray from its accumulated sum; clears the accumulator.
 __device__ __forceinline__ void finalize_ray(float *__restrict__ sacc, const float *__restrict__ proj, int ray,
                                              float w_scale, int linear, float *__restrict__ out_s,
-                                             float *__restrict__ out_res)
+                                             float2 *__restrict__ out_res)
 {
     float sv = sacc[ray] * w_scale;
     sacc[ray] = 0.0f;
     if (out_s) out_s[ray] = sv;
-    if (out_res) out_res[ray] = ray_value(sv, proj[ray], linear);
+    if (out_res) out_res[ray] = ray_term(sv, proj[ray], linear);
 }
 
-// z-mirror store: stored ray r and its mirror; out_res2[r] = {value of r,
-// value of mirror(r)} (the pair the correction gathers in one load).
+// z-mirror store: stored ray r and its mirror m.  The terms are written in
+// both orders, out_res4[r] = {term of r, term of m} and
+// out_res4[r + n_rows] = {term of m, term of r}: a column entry's key is the
+// index of the pair whose first half its own cell sees (and whose second half
+// the cell's mirror sees), so one 16-byte gather serves both cells.
 __device__ __forceinline__ void finalize_pair(float *__restrict__ sacc, const float *__restrict__ proj, int ray,
                                               const Mirror &M, float w_scale, int linear, float *__restrict__ out_s,
-                                              float2 *__restrict__ out_res2)
+                                              float4 *__restrict__ out_res4)
 {
     int rm = mirror_ray(ray, M.n_u, M.n_v);
     float sv = sacc[ray] * w_scale;
@@ -251,8 +264,11 @@ __device__ __forceinline__ void finalize_pair(float *__restrict__ sacc, const fl
         out_s[ray] = sv;
         out_s[rm] = sm;
     }
-    if (out_res2)
-        out_res2[ray] = make_float2(ray_value(sv, proj[ray], linear), ray_value(sm, proj[rm], linear));
+    if (out_res4) {
+        float2 t = ray_term(sv, proj[ray], linear), tm = ray_term(sm, proj[rm], linear);
+        out_res4[ray] = make_float4(t.x, t.y, tm.x, tm.y);
+        out_res4[ray + M.n_rows] = make_float4(tm.x, tm.y, t.x, t.y);
+    }
 }
 
 struct SliceDesc {
@@ -271,17 +287,6 @@ __device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_o
         D.d = 0;
         D.m = 0;
         D.off = 0;
-    }
-}
-
-// One present entry (weight wt > 0) of a cell: a ray with value NaN is
-// skipped; -inf (power rule, P = 0) zeroes the cell, whatever num becomes.
-__device__ __forceinline__ void acc_entry(float wt, float r, float &num, float &den, bool &zero)
-{
-    if (wt > 0.0f && r == r) {
-        zero |= r == -INFINITY;
-        num = fmaf(wt, r, num);
-        den += wt;
     }
 }
 
@@ -306,42 +311,53 @@ __device__ __forceinline__ bool moved_cell(float fv, float nv, const UpdateRule 
 // Per-lane correction sums of one cell (and, MIR, of its mirror cell).
 struct CellSums {
     float num, den, numm, denm;
-    bool zero, zerom;
 };
 
-// rows 0..R-1 of one lane: loads first, then the ray-value gathers.  MIR:
-// the key's bit 31 says whether the cell sees the stored ray (pair .x) or
-// its mirror (pair .y); the mirror cell sees the other one.
-template <typename WT, bool MIR, int R>
-__device__ __forceinline__ void cm_rows(const uint32_t *cray, const WT *cw, const float *res, uint32_t off, int cnt,
-                                        CellSums &S)
+// Adds one column entry of weight w: term = {x, y} of the ray the cell sees
+// (and, MIR, {z, w} of the ray its mirror sees).  Absent rows have w = 0 and
+// a zero term; a stored entry has w > 0 (weights that round to 0 in a
+// reduced-precision store are left out of the cell-major store), so an
+// infinite term never meets a zero weight.
+__device__ __forceinline__ void add_term(float w, float4 t, CellSums &S)
 {
-    uint32_t ry[R];
+    S.num = fmaf(w, t.x, S.num);
+    S.den = fmaf(w, t.y, S.den);
+    S.numm = fmaf(w, t.z, S.numm);
+    S.denm = fmaf(w, t.w, S.denm);
+}
+__device__ __forceinline__ void add_term(float w, float2 t, CellSums &S)
+{
+    S.num = fmaf(w, t.x, S.num);
+    S.den = fmaf(w, t.y, S.den);
+}
+
+// Rows 0..R-1 of one lane (kp, wp: the lane's entry in row 0; row t is
+// t * 32 entries on): loads first, then the ray-term gathers, then the sums.
+// MIR: the key indexes the pair table written by finalize_pair; otherwise
+// the key is the ray and the table holds one term per ray.
+template <typename WT, bool MIR, int R>
+__device__ __forceinline__ void cm_rows(const uint32_t *kp, const WT *wp, const float *res, int cnt, CellSums &S)
+{
+    uint32_t ky[R];
     float wv[R];
 #pragma unroll
     for (int t = 0; t < R; t++) {
         bool in = t < cnt;
-        uint32_t pos = off + (uint32_t)t * kSlice;
-        ry[t] = in ? __ldcs(cray + pos) : 0u;
-        wv[t] = in ? load_cs(cw, pos) : 0.0f;
+        ky[t] = in ? __ldcs(kp + t * kSlice) : 0u;
+        wv[t] = in ? load_cs(wp, t * kSlice) : 0.0f;
     }
     if (MIR) {
+        float4 rv[R];
+#pragma unroll
+        for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg((const float4 *)res + ky[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < R; t++) add_term(wv[t], rv[t], S);
+    } else {
         float2 rv[R];
 #pragma unroll
-        for (int t = 0; t < R; t++)
-            rv[t] = t < cnt ? __ldg((const float2 *)res + (ry[t] & 0x7fffffffu)) : make_float2(0.f, 0.f);
+        for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg((const float2 *)res + ky[t]) : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int t = 0; t < R; t++) {
-            bool up = ry[t] >> 31;
-            acc_entry(wv[t], up ? rv[t].y : rv[t].x, S.num, S.den, S.zero);
-            acc_entry(wv[t], up ? rv[t].x : rv[t].y, S.numm, S.denm, S.zerom);
-        }
-    } else {
-        float rv[R];
-#pragma unroll
-        for (int t = 0; t < R; t++) rv[t] = t < cnt ? __ldg(res + ry[t]) : 0.f;
-#pragma unroll
-        for (int t = 0; t < R; t++) acc_entry(wv[t], rv[t], S.num, S.den, S.zero);
+        for (int t = 0; t < R; t++) add_term(wv[t], rv[t], S);
     }
 }
 
@@ -372,7 +388,7 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
     const WT *cwb = cw + base;
     SliceDesc cur, nxt;
     load_desc(cur, slice_off, base, slice_meta, lane_desc, sl, n_slices, lane);
-    grid_dep_wait();  // the log-ratios and the image belong to the previous kernels
+    grid_dep_wait();  // the ray terms and the image belong to the previous kernels
     for (; sl < n_slices; sl += W) {
         int cnt = (int)(cur.d & 2047u);
         int width = __shfl_sync(0xffffffffu, cnt, 0);
@@ -390,38 +406,34 @@ __device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_o
         if (MIR && cnt > 0) fpv = ((const float2 *)f)[k];
         float fv = MIR ? fpv.x : (cnt > 0 ? *fp : 0.0f);
         float fm = fpv.y;
-        uint32_t off = cur.off + lane;
+        const uint32_t *kp = cr + (cur.off + lane);
+        const WT *wp = cwb + (cur.off + lane);
         load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
-        CellSums S{0.f, 0.f, 0.f, 0.f, false, false};
+        CellSums S{0.f, 0.f, 0.f, 0.f};
         constexpr int RMAX = MIR ? 4 : 8;  // the mirrored form carries two cells: a shorter unroll
         if (width <= 2) {
-            cm_rows<WT, MIR, 2>(cr, cwb, res, off, cnt, S);
+            cm_rows<WT, MIR, 2>(kp, wp, res, cnt, S);
         } else if (width <= 4) {
-            cm_rows<WT, MIR, 4>(cr, cwb, res, off, cnt, S);
+            cm_rows<WT, MIR, 4>(kp, wp, res, cnt, S);
         } else {
-            cm_rows<WT, MIR, RMAX>(cr, cwb, res, off, cnt, S);
+            cm_rows<WT, MIR, RMAX>(kp, wp, res, cnt, S);
             for (int t = RMAX; t < cnt; t++) {  // long columns (cells close to the source)
-                uint32_t pos = off + (uint32_t)t * kSlice;
-                float wt = load_cs(cwb, pos);
-                uint32_t key = __ldcs(cr + pos);
-                if (MIR) {
-                    float2 v = __ldg((const float2 *)res + (key & 0x7fffffffu));
-                    bool up = key >> 31;
-                    acc_entry(wt, up ? v.y : v.x, S.num, S.den, S.zero);
-                    acc_entry(wt, up ? v.x : v.y, S.numm, S.denm, S.zerom);
-                } else {
-                    acc_entry(wt, __ldg(res + key), S.num, S.den, S.zero);
-                }
+                float wt = load_cs(wp, t * kSlice);
+                uint32_t key = __ldcs(kp + t * kSlice);
+                if (MIR) add_term(wt, __ldg((const float4 *)res + key), S);
+                else add_term(wt, __ldg((const float2 *)res + key), S);
             }
         }
+        // a ray with P = 0 has made num -inf (power rule): the cell becomes 0
         bool mv = false;
         if (MIR) {
-            float nx = S.den > 0.0f ? cell_update(fv, S.num, S.den, S.zero, U) : fv;
-            float ny = !pair ? nx : (S.denm > 0.0f ? cell_update(fm, S.numm, S.denm, S.zerom, U) : fm);
+            float nx = S.den > 0.0f ? cell_update(fv, S.num, S.den, S.num == -INFINITY, U) : fv;
+            float ny = !pair ? nx
+                             : (S.denm > 0.0f ? cell_update(fm, S.numm, S.denm, S.numm == -INFINITY, U) : fm);
             if (S.den > 0.0f || (pair && S.denm > 0.0f)) ((float2 *)f)[k] = make_float2(nx, ny);
             mv = moved_cell(fv, nx, U) || moved_cell(fm, ny, U);
         } else if (S.den > 0.0f) {
-            float nv = cell_update(fv, S.num, S.den, S.zero, U);
+            float nv = cell_update(fv, S.num, S.den, S.num == -INFINITY, U);
             *fp = nv;
             mv = moved_cell(fv, nv, U);
         }

@@ -296,9 +296,25 @@ __device__ __forceinline__ int entry_columns(const Mirror &M, int r, uint32_t pc
     return 2;
 }
 
-// one warp per row (coalesced entries)
-__global__ void k_cell_count(const long long *row_ptr, const int *counts, const uint32_t *idx, int n_rows, Mirror M,
-                             const RingEntry *rt, long long cps, int *cell_cnt)
+// weight of a stored entry as a float (the FP16/BF16 stores hold length / w_scale)
+__device__ __forceinline__ float w_as_float(float x) { return x; }
+__device__ __forceinline__ float w_as_float(__half x) { return __half2float(x); }
+__device__ __forceinline__ float w_as_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Cell-major key of a column entry: the index of the ray-term pair the
+// correction gathers -- the stored ray, plus n_rows when the column's cell
+// sees the mirror ray (entry_columns' bit 31).
+__device__ __forceinline__ uint32_t cm_key(uint32_t key, int n_rows)
+{
+    return (key & 0x7fffffffu) + ((key >> 31) ? (uint32_t)n_rows : 0u);
+}
+
+// one warp per row (coalesced entries).  Entries whose stored weight is 0
+// (lengths below the smallest FP16 subnormal) add nothing to a correction
+// and get no column.
+template <typename WT>
+__global__ void k_cell_count(const long long *row_ptr, const int *counts, const uint32_t *idx, const WT *w,
+                             int n_rows, Mirror M, const RingEntry *rt, long long cps, int *cell_cnt)
 {
     long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -306,6 +322,7 @@ __global__ void k_cell_count(const long long *row_ptr, const int *counts, const 
     long long b = row_ptr[ray];
     int n = counts[ray];
     for (int q = lane; q < n; q += 32) {
+        if (!(w_as_float(w[b + q]) > 0.0f)) continue;
         uint32_t col[2], key[2];
         int k = entry_columns(M, (int)ray, idx[b + q], col, key);
         for (int t = 0; t < k; t++) atomicAdd(&cell_cnt[rep_cell_id(rt, cps, col[t])], 1);
@@ -352,6 +369,7 @@ __global__ void k_cell_scatter(const long long *row_ptr, const int *counts, cons
     long long b = row_ptr[ray];
     int n = counts[ray];
     for (int q = wl; q < n; q += 32) {  // one warp per row
+        if (!(w_as_float(w[b + q]) > 0.0f)) continue;  // as k_cell_count
         uint32_t col[2], key[2];
         int k = entry_columns(M, (int)ray, idx[b + q], col, key);
         for (int t = 0; t < k; t++) {
@@ -359,7 +377,7 @@ __global__ void k_cell_scatter(const long long *row_ptr, const int *counts, cons
             long long sl = rep_cell_slice(rt, slices_per_slab, col[t], &lane);
             int slot = atomicAdd(&cell_fill[rep_cell_id(rt, cps, col[t])], 1);
             long long pos = slice_off[sl] + (long long)slot * kSlice + lane;
-            sray[pos] = key[t];
+            sray[pos] = cm_key(key[t], n_rows);
             sw[pos] = w[b + q];
         }
     }
@@ -448,8 +466,8 @@ __global__ void k_set_off(long long *dst, const long long *rel, long long n, lon
 // Sort and lane order in one pass: one warp per slice, each lane owning one
 // cell whose column sits in arrival order at slice_off + 32 t + lane.  The
 // lane's rank (counts falling from lane 0, ties by lane) and count go to
-// lane_desc; the column, sorted by ray key (a total order: a ray meets a cell
-// once per view, its mirror carries bit 31), goes to slots 32 t + rank of the
+// lane_desc; the column, sorted by key (a total order: a ray meets a cell
+// once per view, and a key of its mirror is offset by n_rows), goes to slots 32 t + rank of the
 // lane-ordered store.  Columns of up to kOrderRegs entries are sorted in
 // registers by odd-even transposition; longer ones in place first.
 constexpr int kOrderRegs = 8;
@@ -686,8 +704,9 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
         const int *cn = d_counts + (long long)rep * n_rows;
         USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
-        k_cell_count<<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, n_rows, M, c->d_ring,
-                                                                       c->cells_per_slab, d_cell_cnt);
+        k_cell_count<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, (const WT *)c->d_w,
+                                                                           n_rows, M, c->d_ring, c->cells_per_slab,
+                                                                           d_cell_cnt);
         launch_counter()++;
         int *wd = c->d_slice_width + rep * n_slices;
         uint32_t *md = c->d_slice_meta + rep * n_slices;

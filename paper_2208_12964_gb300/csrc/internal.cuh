@@ -190,7 +190,7 @@ struct uspg_ctx {
     float *d_f = nullptr;
     float *d_proj = nullptr;
     bool have_proj = false;
-    float *d_res = nullptr;  // per-ray log-ratio scratch [n_rays]
+    float *d_res = nullptr;  // per-ray correction terms (float2 [n_rays], or float4 [2 n_rows] mirrored)
     int *d_status = nullptr;
     int *d_sweeps = nullptr;  // [4]: sweeps run, and the per-view Eq. 19 flags (moved, converged)
     cudaStream_t cap_stream = nullptr;
@@ -226,7 +226,7 @@ uspg_status segment_row(uspg_ctx *c, int view, int ray, std::vector<long long> &
 void free_segments(uspg_ctx *c);
 // mart.cu
 struct UpdateRule;
-// linear = 1: the ray values are P/Pbar (Eq. 18) instead of ln(P/Pbar); done
+// linear = 1: the ray terms carry P/Pbar (Eq. 18) instead of ln(P/Pbar); done
 // (device, may be NULL): the per-view kernels do nothing once *done != 0
 uspg_status launch_forward_view(uspg_ctx *c, int view, float *out_s, float *out_res, cudaStream_t s, int linear = 0,
                                 const int *done = nullptr);

@@ -7,15 +7,19 @@
 // representative (Sec. III.C: rotating the source about z moves only the
 // angular position of a segment; slab and ring are unchanged).
 //
-// Per-view simultaneous schedule, two launches per view:
-//   k_forward   one warp per ray streams the ray-major row with 16-byte
-//               loads, gathers the rotated image values and reduces the ray
-//               sum with warp shuffles (Eq. 17); it stores ln(P/Pbar) per ray
-//               (-inf for P = 0, NaN for a ray that is skipped).
-//   k_backward  one warp per 32-cell slice of the cell-major store: each lane
-//               owns one cell, streams its rays and applies
-//               f *= exp(lambda * sum w ln(P/Pbar) / sum w)   (0 if any P = 0).
-//               No atomics: the store is transposed once at build time.
+// Per-view simultaneous schedule, three launches per view:
+//   k_forward_flat      lanes stream 8-entry groups of the ray-major rows with
+//                       16-byte loads, gather the rotated image values and
+//                       combine each ray's partial sums with warp shuffles
+//                       (Eq. 17);
+//   k_forward_finalize  turns each ray sum into the ray's correction term
+//                       {ln(P/Pbar) or P/Pbar, 1} ({0, 0} for a ray that is
+//                       skipped) and clears the accumulator;
+//   k_backward_sell     one warp per 32-cell slice of the cell-major store:
+//                       each lane owns one cell, gathers its rays' terms and
+//                       applies the rule's weighted mean, e.g.
+//                       f *= exp(lambda * sum w ln(P/Pbar) / sum w) (0 if any P = 0).
+//                       No atomics: the store is transposed once at build time.
 // Faithful ray-sequential schedule: k_sequential, one warp that keeps the
 // image in shared memory (or global memory for large grids) and walks
 // iterations -> views -> rays in order, prefetching the next row into
@@ -44,7 +48,7 @@ std::atomic<int64_t> &launch_counter()
 // combined by a segmented shuffle reduction and the first lane of each ray
 // segment adds the partial sum into sacc[ray].  The coefficient stream is
 // read with evict-first loads (__ldcs) so the image stays in L2 across views.
-// k_forward_finalize turns the sums into ln(P/Pbar) and clears sacc.
+// k_forward_finalize turns the sums into correction terms and clears sacc.
 
 // PAIRS: the image is the context's mirrored pair layout; a mirrored store
 // read with a caller's standard-layout image (no-alloc projection) uses
@@ -76,7 +80,7 @@ __global__ void k_forward_finalize(float *__restrict__ sacc, const float *__rest
     grid_dep_wait();
     if (done && *done) return;
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray < n_rays) finalize_ray(sacc, proj, ray, w_scale, linear, out_s, out_res);
+    if (ray < n_rays) finalize_ray(sacc, proj, ray, w_scale, linear, out_s, (float2 *)out_res);
 }
 
 // z-mirror store: one thread per stored ray finalizes it and its mirror
@@ -87,7 +91,7 @@ __global__ void k_forward_finalize_pairs(float *__restrict__ sacc, const float *
     grid_dep_wait();
     if (done && *done) return;
     int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray < M.n_rows) finalize_pair(sacc, proj, ray, M, w_scale, linear, out_s, (float2 *)out_res);
+    if (ray < M.n_rows) finalize_pair(sacc, proj, ray, M, w_scale, linear, out_s, (float4 *)out_res);
 }
 
 // Eq. 19 bookkeeping of a per-view run that may stop early (stop[0] = sweeps
@@ -163,7 +167,8 @@ static int sm_count()
 }
 
 // forward ray sums of one view into acc (cleared on entry, cleared again by
-// the finalize), then out_s = sums and out_res = log-ratios (pairs when mirrored)
+// the finalize), then out_s = sums and out_res = the rays' correction terms
+// (finalize_ray / finalize_pair)
 // f_pairs: f is in the context's image layout (pairs when mirrored); false
 // for a caller's standard-layout image
 template <typename WT>
@@ -562,7 +567,7 @@ static uspg_status fwd_noalloc_typed(uspg_ctx *c, int view, const float *f, floa
     const int TB = 256;
     k_clear_acc<<<(unsigned)((c->n_rays + TB - 1) / TB), TB, 0, s>>>(acc, c->n_rays);
     launch_counter()++;
-    // sums only (no log-ratios): the projections are not read
+    // sums only (no correction terms): the projections are not read
     return fwd_run<WT>(c, view, f, false, acc, out, nullptr, c->d_proj, s);
 }
 
