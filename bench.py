@@ -339,9 +339,10 @@ def roofline(info):
     Per view, with S = entries the representative stores (half of the view's
     nonzeros under the z-mirror), b = index + weight bytes per entry:
       forward:    S*b (rows) + S/8*4 (group rays) + rays*12 (projection in,
-                  ray sum accumulate, log-ratio out); the image gathers hit L2
-      correction: S*b (columns) + slices*76 (offset, meta, lane table)
-                  + cells*8 (image read and write) + rays*4 (log-ratios)
+                  ray sum accumulate, ray term out); the image gathers hit L2
+      correction: S*b (columns) + slices*72 (offset and meta, lane table)
+                  + cells*8 (image read and write) + rays*16 (ray terms: 8 B a ray,
+                  twice with the z-mirror)
     """
     st = info["stats"]
     fw, bw = np.asarray(info["fw"], np.float64), np.asarray(info["bw"], np.float64)
@@ -350,7 +351,7 @@ def roofline(info):
     b_e = 4 + info.get("weight_bytes", 4)
     cells = st["n_cells"]
     fwd_bytes = S * b_e + S / 8 * 4 + n_rays * 12
-    bwd_bytes = S * b_e + st["slices"] * 76 + cells * 8 + n_rays * 4
+    bwd_bytes = S * b_e + st["slices"] * 72 + cells * 8 + n_rays * (16 if st["mirrored"] else 8)
     t_f, t_b = fw.mean(), bw.mean()
     if t_b >= t_f:
         name, b, t = "k_backward", bwd_bytes, t_b

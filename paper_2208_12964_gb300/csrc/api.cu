@@ -47,6 +47,8 @@ static void free_store(uspg_ctx *c)
     cudaFree(c->d_slice_off);
     cudaFree(c->d_slice_meta);
     cudaFree(c->d_slice_width);
+    cudaFree(c->d_slice_desc);
+    c->d_slice_desc = nullptr;
     cudaFree(c->d_sray);
     cudaFree(c->d_sw);
     cudaFree(c->d_counts);
@@ -225,7 +227,7 @@ long long ctx_device_bytes(const uspg_ctx *c)
         b += 8LL * (rows + 1) * 2 + 4LL * rows + 4LL * (rows + 1);                       // row pointers, counts, max
         b += (long long)c->cap_idx * (4 + wb + 8) + 4LL * c->cap_grp;                    // rows, FP64 weights, groups
         b += (long long)c->cap_sell * (4 + wb) + (long long)c->cap_cm * (4 + wb);        // padded and lane-ordered
-        b += slices * (8 + 4 + 4 + 64) + 8LL * c->n_cells + 8LL * (c->slices_per_rep + 1);  // slices, cell scratch
+        b += slices * (8 + 4 + 4 + 8 + 64) + 8LL * c->n_cells + 8LL * (c->slices_per_rep + 1);  // slices, cell scratch
     }
     return b;
 }
@@ -464,7 +466,7 @@ uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
     long long rows = (long long)c->n_reps * c->mir.n_rows;
     long long slices = c->slices_per_rep * c->n_reps;
     o->store_bytes = c->gen.nnz_pad * (4 + wb) + (rows + 1) * 8 + rows * 4 + c->gen.sell_entries * (4 + wb) +
-                     slices * (8 + 4 + 4);
+                     slices * (8 + 64);
     // the same layouts for every view, and without the z-mirror
     double per_view = c->n_reps ? (double)o->store_bytes / c->n_reps : 0.0;
     double unmirrored = c->gen.nnz ? (double)c->gen.nnz_reps_full / (double)c->gen.nnz : 1.0;

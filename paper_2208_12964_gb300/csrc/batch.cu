@@ -27,8 +27,7 @@ struct BatchInst {
     float *sacc;
     float *res;
     const float *proj;
-    const long long *slice_off;
-    const uint32_t *slice_meta;
+    const uint2 *slice_desc;    // [reps * S] {first slot relative to the representative, meta}
     const uint16_t *lane_desc;
     const uint32_t *cray;
     const void *cw;
@@ -80,20 +79,25 @@ __global__ void __launch_bounds__(256, kBwdMinBlocksMirror) k_batch_backward(con
                                                                              long long step, float lambda)
 {
     const BatchInst &I = inst[blockIdx.y];
-    if (step >= I.steps || (int)blockIdx.x >= I.bwd_blocks) return;
+    if (step >= I.steps || (int)blockIdx.x >= I.bwd_blocks) return;  // block-uniform
+    extern __shared__ int4 tab[];
     const UpdateRule U{lambda, 0, 0.0f, nullptr};
     int view = (int)(step % I.n_views);
     int rep = I.view_rep[view];
-    long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long W = ((long long)I.bwd_blocks * blockDim.x) >> 5;
+    fill_tab(tab, I.rt, I.n_rings, I.view_mg[view], threadIdx.x, blockDim.x);
+    __syncthreads();
+    int wg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int W = (I.bwd_blocks * (int)blockDim.x) >> 5;
+    long long base = I.rep_sell[rep];
+    int S = (int)I.S;
     if (I.mir.on)  // block-uniform
-        bwd_slices<WT, true>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
-                             I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt,
-                             I.view_mg[view], I.cps, I.S, U, wg, W, threadIdx.x & 31, I.mir);
+        bwd_slices<WT, true>(I.slice_desc + rep * I.S, I.lane_desc + 32 * rep * I.S, I.cray + base,
+                             (const WT *)I.cw + base, I.res, I.f, tab, (uint32_t)I.cps, S, U, wg, W, threadIdx.x & 31,
+                             I.mir);
     else
-        bwd_slices<WT, false>(I.slice_off + rep * I.S, I.rep_sell[rep], I.slice_meta + rep * I.S,
-                              I.lane_desc + 32 * rep * I.S, I.cray, (const WT *)I.cw, I.res, I.f, I.rt,
-                              I.view_mg[view], I.cps, I.S, U, wg, W, threadIdx.x & 31, I.mir);
+        bwd_slices<WT, false>(I.slice_desc + rep * I.S, I.lane_desc + 32 * rep * I.S, I.cray + base,
+                              (const WT *)I.cw + base, I.res, I.f, tab, (uint32_t)I.cps, S, U, wg, W,
+                              threadIdx.x & 31, I.mir);
 }
 
 }  // namespace uspg
@@ -149,7 +153,7 @@ static cudaError_t enqueue_steps(uspg_batch *b, int mf, int mb, long long s0, lo
     for (long long t = s0; t < s1; t++) {
         k_batch_forward<WT><<<dim3(mf, n), 256, smem, s>>>(b->d_inst, t);
         k_batch_finalize<<<dim3((b->max_rays + 255) / 256, n), 256, 0, s>>>(b->d_inst, t);
-        k_batch_backward<WT><<<dim3(mb, n), 256, 0, s>>>(b->d_inst, t, (float)b->lambda);
+        k_batch_backward<WT><<<dim3(mb, n), 256, smem, s>>>(b->d_inst, t, (float)b->lambda);
         if (nodes) *nodes += 3;
     }
     return cudaGetLastError();
@@ -250,8 +254,7 @@ uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_
         I.sacc = c->d_sacc;
         I.res = c->d_res;
         I.proj = c->d_proj;
-        I.slice_off = c->d_slice_off;
-        I.slice_meta = c->d_slice_meta;
+        I.slice_desc = c->d_slice_desc;
         I.lane_desc = c->d_lane_desc;
         I.cray = c->d_cm_ray;
         I.cw = c->d_cm_w;

@@ -271,25 +271,6 @@ __device__ __forceinline__ void finalize_pair(float *__restrict__ sacc, const fl
     }
 }
 
-struct SliceDesc {
-    uint32_t d, m, off;
-};
-
-__device__ __forceinline__ void load_desc(SliceDesc &D, const long long *slice_off, long long base,
-                                          const uint32_t *slice_meta, const uint16_t *lane_desc, long long sl,
-                                          long long n_slices, int lane)
-{
-    if (sl < n_slices) {
-        D.d = lane_desc[sl * 32 + lane];
-        D.m = slice_meta[sl];
-        D.off = (uint32_t)(slice_off[sl] - base);
-    } else {
-        D.d = 0;
-        D.m = 0;
-        D.off = 0;
-    }
-}
-
 // New value of a cell met by at least one ray (den > 0).  Power rule:
 // f * exp(lambda * num / den), 0 if one of its rays has P = 0; Eq. 18:
 // f * (1 - lambda + lambda * num / den).  The ratio is a weighted mean, so
@@ -361,84 +342,86 @@ __device__ __forceinline__ void cm_rows(const uint32_t *kp, const WT *wp, const 
     }
 }
 
-// The correction is latency-bound (about 1.6 entries per cell and view):
-// 8 resident blocks of 256 threads (32 registers a thread, 64 warps per SM)
-// hide more of it than fewer, fatter warps.
+// The correction is latency-bound (about 1.6 entries per cell and view, at
+// most a few per slice row): 8 resident blocks of 256 threads (32 registers
+// a thread, 64 warps per SM) hide more of it than fewer, fatter warps; rows
+// are unrolled by 2 or 4 (a loop beyond) to stay within those registers.
 constexpr int kBwdMinBlocks = 8;
 constexpr int kBwdMinBlocksMirror = 6;  // the mirrored form holds two cells per lane
 
 // Correction of slices wg, wg + W, ... of one representative (lane-ordered
-// cell-major store): each lane owns one cell; the next slice's descriptor
-// loads are issued before the current slice's gathers; the unrolled row loop
-// is sized per slice from lane 0's (widest) count.  MIR: the store holds the
-// lower-half and middle slabs; a lane also updates the mirror cell (slab
-// n_s-1-s) from the same column, except in the middle slab.
+// cell-major store): each lane owns one cell; the next slice's descriptors
+// are loaded before the current slice's stream; the unrolled row loop is
+// sized per slice from lane 0's (widest) count.  sdesc[s] = {first slot of
+// slice s relative to cray / cw, meta}; lane_desc[32 s + l] = (source lane
+// << 11) | count; tab: ring table {head, ng, shift, 0} of the view.  MIR: the
+// store holds the lower-half and middle slabs; a lane also updates the mirror
+// cell (slab n_s-1-s) from the same column, except in the middle slab.  All
+// index arithmetic is 32-bit (slices * 32 and cell ids are below 2^31).
 template <typename WT, bool MIR>
-__device__ __forceinline__ void bwd_slices(const long long *__restrict__ slice_off, long long base,
-                                           const uint32_t *__restrict__ slice_meta,
-                                           const uint16_t *__restrict__ lane_desc, const uint32_t *__restrict__ cray,
-                                           const WT *__restrict__ cw, const float *__restrict__ res,
-                                           float *__restrict__ f, const RingEntry *__restrict__ rt, int mG,
-                                           long long cps, long long n_slices, const UpdateRule &U, long long wg,
-                                           long long W, int lane, const Mirror &M)
+__device__ __forceinline__ void bwd_slices(const uint2 *__restrict__ sdesc, const uint16_t *__restrict__ lane_desc,
+                                           const uint32_t *__restrict__ cray, const WT *__restrict__ cw,
+                                           const float *__restrict__ res, float *__restrict__ f, const int4 *tab,
+                                           uint32_t cps, int n_slices, const UpdateRule &U, int wg, int W, int lane,
+                                           const Mirror &M)
 {
-    long long sl = wg;
+    int sl = wg;
     if (sl >= n_slices) return;
-    const uint32_t *cr = cray + base;
-    const WT *cwb = cw + base;
-    SliceDesc cur, nxt;
-    load_desc(cur, slice_off, base, slice_meta, lane_desc, sl, n_slices, lane);
+    uint2 dn = sdesc[sl];
+    uint32_t ln = lane_desc[sl * kSlice + lane];
     grid_dep_wait();  // the ray terms and the image belong to the previous kernels
     for (; sl < n_slices; sl += W) {
-        int cnt = (int)(cur.d & 2047u);
-        int width = __shfl_sync(0xffffffffu, cnt, 0);
-        RingEntry re = rt[cell_ring(cur.m)];
-        int sec = cell_sector(cur.m) + (int)(cur.d >> 11);
-        int s2 = sec + mG * re.step;
-        s2 = s2 >= re.ng ? s2 - re.ng : s2;
-        // cell ids are below 2^31 (checked at context creation): 32-bit index math
-        int slab = cell_slab(cur.m);
-        uint32_t within = (uint32_t)re.head + (uint32_t)s2;
-        uint32_t k = slab * (uint32_t)cps + within;  // MIR: the pair {cell, mirror cell} of the image
-        float *fp = f + k;
-        bool pair = MIR && 2 * slab != M.n_slabs - 1;  // the middle slab is its own mirror
-        float2 fpv = make_float2(0.0f, 0.0f);
-        if (MIR && cnt > 0) fpv = ((const float2 *)f)[k];
-        float fv = MIR ? fpv.x : (cnt > 0 ? *fp : 0.0f);
-        float fm = fpv.y;
-        const uint32_t *kp = cr + (cur.off + lane);
-        const WT *wp = cwb + (cur.off + lane);
-        load_desc(nxt, slice_off, base, slice_meta, lane_desc, sl + W, n_slices, lane);
+        const uint2 dc = dn;
+        const uint32_t lc = ln;
+        if (sl + W < n_slices) {
+            dn = sdesc[sl + W];
+            ln = lane_desc[(sl + W) * kSlice + lane];
+        }
+        const int cnt = (int)(lc & 2047u);
+        const int width = __shfl_sync(0xffffffffu, cnt, 0);
+        const int4 t = tab[cell_ring(dc.y)];
+        int sec = cell_sector(dc.y) + (int)(lc >> 11) + t.z;
+        sec = sec >= t.y ? sec - t.y : sec;
+        const int slab = cell_slab(dc.y);
+        const uint32_t k = (uint32_t)slab * cps + (uint32_t)(t.x + sec);  // MIR: the pair {cell, mirror cell}
+        const bool pair = MIR && 2 * slab != M.n_slabs - 1;                // the middle slab is its own mirror
+        float fv = 0.0f, fm = 0.0f;
+        if (cnt > 0) {
+            if (MIR) {
+                float2 v = ((const float2 *)f)[k];
+                fv = v.x;
+                fm = v.y;
+            } else {
+                fv = f[k];
+            }
+        }
+        const uint32_t *kp = cray + (dc.x + lane);
+        const WT *wp = cw + (dc.x + lane);
         CellSums S{0.f, 0.f, 0.f, 0.f};
-        constexpr int RMAX = MIR ? 4 : 8;  // the mirrored form carries two cells: a shorter unroll
         if (width <= 2) {
             cm_rows<WT, MIR, 2>(kp, wp, res, cnt, S);
-        } else if (width <= 4) {
-            cm_rows<WT, MIR, 4>(kp, wp, res, cnt, S);
         } else {
-            cm_rows<WT, MIR, RMAX>(kp, wp, res, cnt, S);
-            for (int t = RMAX; t < cnt; t++) {  // long columns (cells close to the source)
-                float wt = load_cs(wp, t * kSlice);
-                uint32_t key = __ldcs(kp + t * kSlice);
+            cm_rows<WT, MIR, 4>(kp, wp, res, cnt, S);
+            for (int r = 4; r < cnt; r++) {  // long columns (cells close to the source)
+                float wt = load_cs(wp, r * kSlice);
+                uint32_t key = __ldcs(kp + r * kSlice);
                 if (MIR) add_term(wt, __ldg((const float4 *)res + key), S);
                 else add_term(wt, __ldg((const float2 *)res + key), S);
             }
         }
         // a ray with P = 0 has made num -inf (power rule): the cell becomes 0
-        bool mv = false;
+        float nx = S.den > 0.0f ? cell_update(fv, S.num, S.den, S.num == -INFINITY, U) : fv;
+        float ny = fm;
         if (MIR) {
-            float nx = S.den > 0.0f ? cell_update(fv, S.num, S.den, S.num == -INFINITY, U) : fv;
-            float ny = !pair ? nx
-                             : (S.denm > 0.0f ? cell_update(fm, S.numm, S.denm, S.numm == -INFINITY, U) : fm);
+            ny = !pair ? nx : (S.denm > 0.0f ? cell_update(fm, S.numm, S.denm, S.numm == -INFINITY, U) : fm);
             if (S.den > 0.0f || (pair && S.denm > 0.0f)) ((float2 *)f)[k] = make_float2(nx, ny);
-            mv = moved_cell(fv, nx, U) || moved_cell(fm, ny, U);
         } else if (S.den > 0.0f) {
-            float nv = cell_update(fv, S.num, S.den, S.num == -INFINITY, U);
-            *fp = nv;
-            mv = moved_cell(fv, nv, U);
+            f[k] = nx;
         }
-        if (U.tol > 0.0f && __any_sync(0xffffffffu, mv) && lane == 0) *U.moved = 1;
-        cur = nxt;
+        if (U.tol > 0.0f) {  // Eq. 19 (uniform branch)
+            bool mv = moved_cell(fv, nx, U) || (MIR && moved_cell(fm, ny, U));
+            if (__any_sync(0xffffffffu, mv) && lane == 0) *U.moved = 1;
+        }
     }
 }
 

@@ -557,6 +557,15 @@ __global__ void k_cell_order(long long n_slices, const uint32_t *meta, const lon
     }
 }
 
+// Correction descriptors of one representative's slices: {first slot
+// relative to the representative's base, meta}, one 8-byte load per slice.
+__global__ void k_slice_desc(uint2 *desc, const long long *slice_off, const uint32_t *meta, long long base,
+                             long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) desc[i] = make_uint2((uint32_t)(slice_off[i] - base), meta[i]);
+}
+
 // ray of every aligned group of kRowPad entries of the ray-major store (rows
 // start and end on group boundaries, so a group never straddles two rays)
 __global__ void k_group_rays(const long long *row_ptr, long long n_all, int n_rows, uint32_t *grp_ray)
@@ -620,6 +629,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_rel, sizeof(long long) * (n_slices + 1)));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_off, sizeof(long long) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_meta, sizeof(uint32_t) * n_slices * nreps));
+        USPG_CUDA(c, cudaMalloc(&c->d_slice_desc, sizeof(uint2) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_width, sizeof(int) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_stats, sizeof(long long) * (2 * nreps + 1)));
         c->store_moved = true;
@@ -694,6 +704,8 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                                      cudaMemcpyDeviceToHost, s));
 
     // cell-major store, one representative at a time
+    if (n_slices * kSlice >= (1LL << 31))
+        return fail(c, USPG_EUNSUPPORTED, "a view's cell-major store has 2^26 slices or more");
     int *d_cell_cnt = c->d_cell_cnt, *d_cell_fill = c->d_cell_fill;
     long long *d_rel = c->d_rel;
     // pass 1: slice widths and offsets (every representative's slots follow
@@ -777,6 +789,10 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         k_cell_scatter<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(
             rp, cn, c->d_idx, (const WT *)c->d_w, n_rows, M, c->d_ring, c->cells_per_slab, c->slices_per_slab, so,
             d_cell_fill, c->d_sray, (WT *)c->d_sw);
+        launch_counter()++;
+        k_slice_desc<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_desc + rep * n_slices, so,
+                                                         c->d_slice_meta + rep * n_slices, c->h_sell_base[rep],
+                                                         n_slices);
         launch_counter()++;
         // the scatter's slot counters now hold every cell's count
         k_cell_order<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(

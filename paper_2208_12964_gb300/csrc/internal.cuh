@@ -160,6 +160,7 @@ struct uspg_ctx {
     float *d_rowmax = nullptr;
     long long *d_slice_off = nullptr;
     uint32_t *d_slice_meta = nullptr;
+    uint2 *d_slice_desc = nullptr;  // [reps][slices] {first slot relative to the representative, meta}
     int *d_slice_width = nullptr;
     uint32_t *d_sray = nullptr;
     void *d_sw = nullptr;

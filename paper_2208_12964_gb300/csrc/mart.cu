@@ -125,19 +125,21 @@ __global__ void k_sweep_end(int *stop)
 // is sized per slice (warp-uniform) to 2, 4 or 8 rows, with a loop beyond.
 template <typename WT, bool MIR>
 __global__ void __launch_bounds__(256, MIR ? kBwdMinBlocksMirror : kBwdMinBlocks)
-    k_backward_sell(const long long *__restrict__ slice_off, long long base, const uint32_t *__restrict__ slice_meta,
-                    const uint16_t *__restrict__ lane_desc, const uint32_t *__restrict__ cray,
-                    const WT *__restrict__ cw, const float *__restrict__ res, float *__restrict__ f,
-                    const RingEntry *__restrict__ rt, int mG, long long cps, long long n_slices, UpdateRule U,
-                    Mirror M, const int *__restrict__ done)
+    k_backward_sell(const uint2 *__restrict__ sdesc, const uint16_t *__restrict__ lane_desc,
+                    const uint32_t *__restrict__ cray, const WT *__restrict__ cw, const float *__restrict__ res,
+                    float *__restrict__ f, const RingEntry *__restrict__ rt, int n_rings, int mG, long long cps,
+                    int n_slices, UpdateRule U, Mirror M, const int *__restrict__ done)
 {
+    extern __shared__ int4 tab[];
+    fill_tab(tab, rt, n_rings, mG, threadIdx.x, blockDim.x);
+    __syncthreads();
     if (done) {
         grid_dep_wait();
         if (*done) return;
     }
-    bwd_slices<WT, MIR>(slice_off, base, slice_meta, lane_desc, cray, cw, res, f, rt, mG, cps, n_slices, U,
-                        ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                        ((long long)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, M);
+    bwd_slices<WT, MIR>(sdesc, lane_desc, cray, cw, res, f, tab, (uint32_t)cps, n_slices, U,
+                        (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), (int)((gridDim.x * blockDim.x) >> 5),
+                        threadIdx.x & 31, M);
 }
 
 // Launch with programmatic stream serialization (see grid_dep_wait).
@@ -236,20 +238,19 @@ static uspg_status bwd_typed(uspg_ctx *c, int view, const UpdateRule &U, const i
     long long grid = std::min<long long>(want, (long long)sm_count() * per_sm);
     if (grid < 1) grid = 1;
     long long base = c->h_sell_base[rep];
-    const long long *so = c->d_slice_off + rep * S;
-    const uint32_t *meta = c->d_slice_meta + rep * S;
+    const uint2 *sd = c->d_slice_desc + rep * S;
     const uint16_t *ld = c->d_lane_desc + 32 * rep * S;
-    const WT *cw = (const WT *)c->d_cm_w;
+    const uint32_t *cr = (const uint32_t *)c->d_cm_ray + base;
+    const WT *cw = (const WT *)c->d_cm_w + base;
     const float *res = c->d_res;
+    size_t smem = sizeof(int4) * c->n_rings;
     cudaError_t e;
     if (c->mir.on)
-        e = launch_pdl(k_backward_sell<WT, true>, (unsigned)grid, TB, 0, s, so, base, meta, ld,
-                       (const uint32_t *)c->d_cm_ray, cw, res, c->d_f, (const RingEntry *)c->d_ring, mG,
-                       c->cells_per_slab, S, U, c->mir, done);
+        e = launch_pdl(k_backward_sell<WT, true>, (unsigned)grid, TB, smem, s, sd, ld, cr, cw, res, c->d_f,
+                       (const RingEntry *)c->d_ring, c->n_rings, mG, c->cells_per_slab, (int)S, U, c->mir, done);
     else
-        e = launch_pdl(k_backward_sell<WT, false>, (unsigned)grid, TB, 0, s, so, base, meta, ld,
-                       (const uint32_t *)c->d_cm_ray, cw, res, c->d_f, (const RingEntry *)c->d_ring, mG,
-                       c->cells_per_slab, S, U, c->mir, done);
+        e = launch_pdl(k_backward_sell<WT, false>, (unsigned)grid, TB, smem, s, sd, ld, cr, cw, res, c->d_f,
+                       (const RingEntry *)c->d_ring, c->n_rings, mG, c->cells_per_slab, (int)S, U, c->mir, done);
     launch_counter()++;
     USPG_CUDA(c, e);
     return USPG_OK;

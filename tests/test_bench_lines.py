@@ -26,7 +26,7 @@ def test_roofline_is_algorithmic_bytes_over_mean_launch_time():
     info = _info(0.027, 0.033)
     r = bench.roofline(info)
     S = 77217546 / 15
-    bwd = S * 8 + 102912 * 76 + 6340608 * 8 + 65536 * 4
+    bwd = S * 8 + 102912 * 72 + 6340608 * 8 + 65536 * 16
     assert r["kernel"] == "k_backward" and r["bytes_per_launch"] == int(bwd)
     assert abs(r["achieved"] - bwd / 0.033e-3 / 1e9) < 0.1
     peak, src = bench.load_peaks()
