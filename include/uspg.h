@@ -150,6 +150,8 @@ typedef struct {
     int64_t gcd;               /* rotational symmetry order G of the grid */
     int64_t mirrored;          /* 1: z-mirror store (only the lower detector rows and slabs are held) */
     int64_t slices;            /* cell-major slices (32 cells) per representative */
+    int64_t walked_rows;       /* representative rows the FP64 walk traced; the rest are mirror images
+                                  (transverse symmetry, Sec. III.C) of traced rows */
 } uspg_stats;
 
 /* --- context -------------------------------------------------------------- */
@@ -172,11 +174,16 @@ uspg_status uspg_sync(uspg_ctx *ctx, uspg_stream stream);
 
 /* --- coefficients (Sec. III.A-C, Algorithm 1) -------------------------------- */
 
-/* REPRESENTATIVES: traces every ray of every representative view in FP64
+/* REPRESENTATIVES: traces the rays of the representative views in FP64
  * (cylinder roots of Eq. 3-4 formed as (mr-d)(mr+d), axial and radial plane
  * crossings, midpoint cell assignment of Eq. 5-10, pieces < 1e-9 of a cell
  * dropped, repeated cells merged) and stores the rows twice: ray-major for the
  * forward ray sums and cell-major for the correction.
+ * Rows that are mirror images of others under the reflection about the
+ * source axis (the paper's quarter symmetry of the first view's lines, Sec.
+ * III.C: column u <-> -u, azimuth phi <-> -phi) are derived instead of traced;
+ * a row with a piece whose cell decision lies within 1e-7 of a sector
+ * boundary or 1e-3 ring widths of the axis is traced directly either way.
  * SEGMENTS: traces the first view's rays only, to their cylinder and
  * axial-plane crossings (no radial planes, Sec. III.B), and stores each
  * segment's ring, slab and end azimuths (64-bit fixed turns); an end azimuth

@@ -68,6 +68,11 @@ static void free_store(uspg_ctx *c)
     c->d_grp_ray = nullptr;
     c->cap_grp = 0;
     cudaFree(c->d_w64);
+    cudaFree(c->d_plan);
+    cudaFree(c->d_tied);
+    cudaFree(c->d_retrace);
+    c->d_plan = c->d_tied = nullptr;
+    c->d_retrace = nullptr;
     c->d_counts = c->d_rep_view = c->d_cell_cnt = c->d_cell_fill = nullptr;
     c->d_rel = nullptr;
     c->d_stats = nullptr;
@@ -458,6 +463,7 @@ uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
         o->gcd = c->G;
         o->mirrored = 0;
         o->slices = 0;
+        o->walked_rows = c->n_rays;
         return USPG_OK;
     }
     o->n_reps = c->n_reps;
@@ -475,6 +481,7 @@ uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
     o->gcd = c->G;
     o->mirrored = c->mir.on;
     o->slices = c->slices_per_rep;
+    o->walked_rows = c->gen_walked_rows;
     return USPG_OK;
 }
 

@@ -27,6 +27,7 @@
 #include "walk.cuh"
 
 #include <algorithm>
+#include <map>
 
 namespace uspg {
 
@@ -43,41 +44,67 @@ __global__ void k_boundaries(const RingEntry *rt, int n_rings, double2 *bdir, fl
     }
 }
 
-// Upper bound on each row's length from the FP32 sizing walk.
-__global__ void __launch_bounds__(128) k_size(Geometry g, const RingEntry *rt, const float2 *bdirf,
-                                              const int *rep_view, int n_reps, int *caps)
+// ---- which rows are traced -------------------------------------------------
+//
+// Transverse symmetry (Sec. III.C: a quarter of the first view's lines
+// suffice): the reflection y -> -y fixes the source axis and maps view theta
+// onto view -theta, detector column a onto n_u-1-a (fan and cone; a parallel
+// ray keeps its bin, reversed), and sector j of every ring onto sector
+// -1-j (mod n_g).  Representatives pair up as (rho, 1/G - rho): the rows of
+// one are the mirror images of the other's, rotated by whole 1/G turns.  A
+// representative that is its own mirror (rho = 0 or 1/(2G); fan or cone)
+// traces the columns 2a <= n_u-1 and mirrors the rest.  The walks run over a
+// list of traced representatives; every other row is derived (k_derive).
+struct TracePlan {
+    const int *reps;  // [n] representatives whose rows are walked
+    int n;
+    const int *half;  // [n_reps] 1: walk only the columns 2a <= n_u-1
+};
+
+// mirror column of a stored ray: fan and cone flip the detector column
+__host__ __device__ inline int mirror_column(const Geometry &g, int ray)
 {
-    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)n_reps * g.n_rows) return;
+    if (g.geometry == USPG_PARALLEL_2D) return ray;
+    int a = ray % g.n_u;
+    return ray - a + (g.n_u - 1 - a);
+}
+
+__device__ __forceinline__ bool walked(const Geometry &g, const TracePlan &P, long long gid, int *rep, int *ray)
+{
+    if (gid >= (long long)P.n * g.n_rows) return false;
     // neighbouring threads trace the same ray in different representative
     // views: rotations about the axis, so the same rings and slabs and nearly
     // the same sector crossings -- the walks of a warp stay in step
-    int rep = (int)(gid % n_reps), ray = (int)(gid / n_reps);
-    long long row = (long long)rep * g.n_rows + ray;
-    caps[row] = size_ray(g, rt, bdirf, rep_view[rep], ray);
+    *rep = P.reps[gid % P.n];
+    *ray = (int)(gid / P.n);
+    return !(P.half[*rep] && 2 * (*ray % g.n_u) > g.n_u - 1);
+}
+
+// Upper bound on each walked row's length from the FP32 sizing walk.
+__global__ void __launch_bounds__(128) k_size(Geometry g, const RingEntry *rt, const float2 *bdirf,
+                                              const int *rep_view, TracePlan P, int *caps)
+{
+    int rep, ray;
+    if (!walked(g, P, (long long)blockIdx.x * blockDim.x + threadIdx.x, &rep, &ray)) return;
+    caps[(long long)rep * g.n_rows + ray] = size_ray(g, rt, bdirf, rep_view[rep], ray);
 }
 
 // Exact row lengths (the FP64 walk without storing); used only when a row
 // outgrew its FP32 bound.
 template <int MAXR>
 __global__ void __launch_bounds__(128) k_count(Geometry g, const RingEntry *rt, const double2 *bdir,
-                                               const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
+                                               const float2 *bdirf, const int *rep_view, TracePlan P, int *counts,
                                                int *status)
 {
-    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)n_reps * g.n_rows) return;
-    // neighbouring threads trace the same ray in different representative
-    // views: rotations about the axis, so the same rings and slabs and nearly
-    // the same sector crossings -- the walks of a warp stay in step
-    int rep = (int)(gid % n_reps), ray = (int)(gid / n_reps);
-    long long row = (long long)rep * g.n_rows + ray;
+    int rep, ray;
+    if (!walked(g, P, (long long)blockIdx.x * blockDim.x + threadIdx.x, &rep, &ray)) return;
     uint32_t in_cell[MAXR];
     double root[MAXR];
     CountSink sink;
     sink.in_cell = in_cell;
     sink.root = root;
     walk_ray(g, rt, bdir, bdirf, rep_view[rep], ray, sink, status);
-    counts[row] = sink.n;
+    counts[(long long)rep * g.n_rows + ray] = sink.n;
 }
 
 // ---- stored precision -----------------------------------------------------
@@ -120,19 +147,25 @@ __device__ float store_row(const double *w64, long long b, long long e, int n, i
 // FP64 walk into the row's slots [row_ptr[i], row_ptr[i+1]); writes the
 // entry count to counts[i], pads the rest of the row (cell 0, weight 0), and
 // stores the row in the stored precision with its largest weight.  A row
-// with more entries than slots raises kStatusCountMismatch.
+// with more entries than slots raises kStatusCountMismatch.  The rows are
+// the walked rows of plan P, or (list != NULL) the rows list[0 .. *n_list);
+// tied (optional) receives each row's tie flag (classify_exact).
 template <int MAXR>
 __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, const double2 *bdir,
-                                              const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
+                                              const float2 *bdirf, const int *rep_view, TracePlan P,
+                                              const long long *list, const int *n_list, int *counts,
                                               const long long *row_ptr, uint32_t *idx, double *w64, int *status,
-                                              int dtype, double inv_scale, void *w, float *rowmax)
+                                              int dtype, double inv_scale, void *w, float *rowmax, int *tied)
 {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)n_reps * g.n_rows) return;
-    // neighbouring threads trace the same ray in different representative
-    // views: rotations about the axis, so the same rings and slabs and nearly
-    // the same sector crossings -- the walks of a warp stay in step
-    int rep = (int)(gid % n_reps), ray = (int)(gid / n_reps);
+    int rep, ray;
+    if (list) {
+        if (gid >= *n_list) return;
+        rep = (int)(list[gid] / g.n_rows);
+        ray = (int)(list[gid] % g.n_rows);
+    } else if (!walked(g, P, gid, &rep, &ray)) {
+        return;
+    }
     long long row = (long long)rep * g.n_rows + ray;
     long long b = row_ptr[row], e = row_ptr[row + 1];
     uint32_t in_cell[MAXR];
@@ -148,6 +181,7 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
     walk_ray(g, rt, bdir, bdirf, rep_view[rep], ray, sink, status);
     if (sink.overflow) flag(status, kStatusCountMismatch);
     counts[row] = sink.n;
+    if (tied) tied[row] = sink.tied;
     for (long long q = b + sink.n; q < e; q++) {
         idx[q] = 0;
         w64[q] = 0.0;
@@ -160,6 +194,70 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
     rowmax[row] = mx;
 }
 
+// Source row of a derived row (rep, ray), or -1 for a walked row.
+__device__ __forceinline__ long long derive_source(const Geometry &g, const int *rep_src, const int *half, int rep,
+                                                   int ray)
+{
+    int src = rep_src[rep];
+    if (src < 0 && !(half[rep] && 2 * (ray % g.n_u) > g.n_u - 1)) return -1;
+    if (src < 0) src = rep;
+    return (long long)src * g.n_rows + mirror_column(g, ray);
+}
+
+// Bounds of the derived rows: the source row's FP32 bound (a mirror image
+// has the source's length), with a little slack for a row that is walked
+// after all because its source is tied.
+__global__ void k_derive_caps(Geometry g, int n_reps, const int *rep_src, const int *half, int *caps)
+{
+    long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (long long)n_reps * g.n_rows) return;
+    long long src = derive_source(g, rep_src, half, (int)(row / g.n_rows), (int)(row % g.n_rows));
+    if (src >= 0) caps[row] = caps[src] + 4;
+}
+
+// One warp per derived row: the source row mirrored (sector j -> (shift -
+// 1 - j) mod n_g with shift = M n_g / G, M = rep_shift[rep]; slab and ring
+// and weights unchanged), or, when the source row is tied, the row is queued
+// for the direct walk (retrace).
+template <typename WT>
+__global__ void k_derive(Geometry g, const RingEntry *rt, int n_reps, const int *rep_src, const int *half,
+                         const int *rep_shift, const long long *row_ptr, int *counts, uint32_t *idx, double *w64,
+                         WT *w, float *rowmax, const int *tied, long long *retrace, int *n_retrace)
+{
+    long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= (long long)n_reps * g.n_rows) return;
+    int rep = (int)(row / g.n_rows);
+    long long src = derive_source(g, rep_src, half, rep, (int)(row % g.n_rows));
+    if (src < 0) return;
+    if (tied[src]) {
+        if (lane == 0) retrace[atomicAdd(n_retrace, 1)] = row;
+        return;
+    }
+    int n = counts[src];
+    long long sb = row_ptr[src], db = row_ptr[row], de = row_ptr[row + 1];
+    int M = rep_shift[rep];
+    for (long long q = lane; q < de - db; q += 32) {
+        if (q < n) {
+            uint32_t pc = idx[sb + q];
+            int ring = cell_ring(pc), ng = rt[ring].ng;
+            int sec = M * rt[ring].step - 1 - cell_sector(pc);
+            sec = sec < 0 ? sec + ng : sec;
+            idx[db + q] = pack_cell(cell_slab(pc), ring, sec);
+            w64[db + q] = w64[sb + q];
+            w[db + q] = w[sb + q];
+        } else {
+            idx[db + q] = 0;
+            w64[db + q] = 0.0;
+            w[db + q] = to_w<WT>(0.0f);
+        }
+    }
+    if (lane == 0) {
+        counts[row] = n;
+        rowmax[row] = rowmax[src];
+    }
+}
+
 // what k_fill writes besides the FP64 rows: stored weights and row maxima
 struct FillOut {
     int dtype;
@@ -168,24 +266,33 @@ struct FillOut {
     float *rowmax;
 };
 
+// what a walk reads besides the geometry: the rows to walk (a plan, or a
+// list whose length is on the device) and where the tie flags go
+struct WalkRows {
+    TracePlan plan;
+    const long long *list = nullptr;
+    const int *n_list = nullptr;
+    int *tied = nullptr;
+};
+
 template <int MAXR>
 static void launch_walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
-                        const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
-                        const long long *row_ptr, uint32_t *idx, double *w64, int *status, const FillOut &fo)
+                        const double2 *bdir, const float2 *bdirf, const int *rep_view, const WalkRows &wr,
+                        int *counts, const long long *row_ptr, uint32_t *idx, double *w64, int *status,
+                        const FillOut &fo)
 {
     if (fill)
-        k_fill<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status,
-                                          fo.dtype, fo.inv_scale, fo.w, fo.rowmax);
+        k_fill<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, wr.plan, wr.list, wr.n_list, counts, row_ptr,
+                                          idx, w64, status, fo.dtype, fo.inv_scale, fo.w, fo.rowmax, wr.tied);
     else
-        k_count<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, n_reps, counts, status);
+        k_count<MAXR><<<grid, 128, 0, s>>>(g, rt, bdir, bdirf, rep_view, wr.plan, counts, status);
 }
 
 static void walk(bool fill, unsigned grid, cudaStream_t s, const Geometry &g, const RingEntry *rt,
-                 const double2 *bdir, const float2 *bdirf, const int *rep_view, int n_reps, int *counts,
+                 const double2 *bdir, const float2 *bdirf, const int *rep_view, const WalkRows &wr, int *counts,
                  const long long *row_ptr, uint32_t *idx, double *w64, int *status, const FillOut &fo = FillOut{})
 {
-#define USPG_WALK(M) \
-    launch_walk<M>(fill, grid, s, g, rt, bdir, bdirf, rep_view, n_reps, counts, row_ptr, idx, w64, status, fo)
+#define USPG_WALK(M) launch_walk<M>(fill, grid, s, g, rt, bdir, bdirf, rep_view, wr, counts, row_ptr, idx, w64, status, fo)
     if (g.n_rings <= 64) USPG_WALK(64);
     else if (g.n_rings <= 128) USPG_WALK(128);
     else if (g.n_rings <= 256) USPG_WALK(256);
@@ -608,6 +715,55 @@ cudaError_t scan_counts(const int *in, long long n, long long *out, cudaStream_t
     return exclusive_scan<int>(in, n, 1, out, s);
 }
 
+// Host side of the transverse symmetry: which representatives are walked,
+// which are mirror images of which (and by how many 1/G turns the mirror
+// image is rotated), which walk only half their columns.  View k sits at
+// theta = (m + key / den) / G turns (m = floor(k arc G / den)); the mirror of
+// residue key is residue (den - key) mod den.
+struct SymPlan {
+    std::vector<int> trace, half, src, shift;
+    long long walked_rows = 0;
+};
+
+static SymPlan sym_plan(const uspg_ctx *c)
+{
+    const int nreps = c->n_reps;
+    const long long den = c->scan.arc_den * (long long)c->scan.n_views;
+    std::vector<long long> key(nreps), m(nreps);
+    std::map<long long, int> rep_of_key;
+    for (int r = 0; r < nreps; r++) {
+        long long num = (long long)c->rep_view[r] * c->scan.arc_num * c->G;
+        m[r] = num / den;
+        key[r] = num % den;
+        rep_of_key[key[r]] = r;
+    }
+    SymPlan P;
+    P.half.assign(nreps, 0);
+    P.src.assign(nreps, -1);
+    P.shift.assign(nreps, 0);
+    const bool columns_mirror = c->scan.geometry != USPG_PARALLEL_2D;  // a parallel ray is its own mirror
+    for (int r = 0; r < nreps; r++) {
+        if (P.src[r] >= 0) continue;  // a mirror image of an earlier representative
+        auto it = rep_of_key.find((den - key[r]) % den);
+        if (it != rep_of_key.end()) {
+            int r2 = it->second;
+            int M = (int)((m[r] + m[r2] + (key[r] != 0 ? 1 : 0)) % c->G);
+            if (r2 == r && columns_mirror) {
+                P.half[r] = 1;
+                P.shift[r] = M;
+            } else if (r2 > r) {
+                P.src[r2] = r;
+                P.shift[r2] = M;
+            }
+        }
+        P.trace.push_back(r);
+    }
+    int n_u = c->scan.n_u, half_cols = 0;
+    for (int a = 0; a < n_u; a++) half_cols += 2 * a <= n_u - 1;
+    for (int r : P.trace) P.walked_rows += P.half[r] ? (long long)c->mir.n_rows / n_u * half_cols : c->mir.n_rows;
+    return P;
+}
+
 template <typename WT>
 static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
 {
@@ -632,21 +788,52 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_slice_desc, sizeof(uint2) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_width, sizeof(int) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_stats, sizeof(long long) * (2 * nreps + 1)));
+        // symmetry plan tables, tie flags, rows to walk after all
+        USPG_CUDA(c, cudaMalloc(&c->d_plan, sizeof(int) * 6 * nreps));
+        USPG_CUDA(c, cudaMalloc(&c->d_tied, sizeof(int) * (nrows + 1)));
+        USPG_CUDA(c, cudaMalloc(&c->d_retrace, sizeof(long long) * (nrows + 1)));
         c->store_moved = true;
     }
     int *d_rep_view = c->d_rep_view, *d_counts = c->d_counts;
 
     const int TB = 128;
     // with the z-mirror only the rows of rays 0 .. n_rows-1 (lower detector rows) are traced and stored
+    // symmetry plan: d_plan = {walked reps, half, source, shift, all reps, zeros}
+    SymPlan sp = sym_plan(c);
+    {
+        std::vector<int> tab(6 * nreps, 0);
+        for (size_t q = 0; q < sp.trace.size(); q++) tab[q] = sp.trace[q];
+        for (int r = 0; r < nreps; r++) {
+            tab[nreps + r] = sp.half[r];
+            tab[2 * nreps + r] = sp.src[r];
+            tab[3 * nreps + r] = sp.shift[r];
+            tab[4 * nreps + r] = r;
+        }
+        USPG_CUDA(c, cudaMemcpyAsync(c->d_plan, tab.data(), sizeof(int) * 6 * nreps, cudaMemcpyHostToDevice, s));
+    }
+    const int *d_trace = c->d_plan, *d_half = c->d_plan + nreps, *d_src = c->d_plan + 2 * nreps;
+    const int *d_shift = c->d_plan + 3 * nreps, *d_all = c->d_plan + 4 * nreps, *d_zero = c->d_plan + 5 * nreps;
+    const bool sym = sp.walked_rows < nrows;
+    int *d_n_retrace = c->d_tied + nrows;  // counter after the flags
     // rows sized by the FP32 bound, filled by the FP64 walk; if any row
-    // outgrows its bound the exact FP64 count sizes the rows instead
+    // outgrows its bound the exact FP64 count sizes the rows instead (and
+    // every row is walked)
     long long nnz_pad = 0;
+    c->gen_walked_rows = nrows;
     for (int attempt = 0; attempt < 2; attempt++) {
+        const bool use_sym = attempt == 0 && sym;
+        WalkRows wr;
+        wr.plan = use_sym ? TracePlan{d_trace, (int)sp.trace.size(), d_half} : TracePlan{d_all, nreps, d_zero};
+        const unsigned grid = nblk((long long)wr.plan.n * n_rows, TB);
         if (attempt == 0) {
-            k_size<<<nblk(nrows, TB), TB, 0, s>>>(g, c->d_ring, c->d_bdirf, d_rep_view, nreps, d_counts);
+            k_size<<<grid, TB, 0, s>>>(g, c->d_ring, c->d_bdirf, d_rep_view, wr.plan, d_counts);
+            if (use_sym) {
+                launch_counter()++;
+                k_derive_caps<<<nblk(nrows, 256), 256, 0, s>>>(g, nreps, d_src, d_half, d_counts);
+            }
         } else {
-            walk(false, nblk(nrows, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, nreps, d_counts,
-                 nullptr, nullptr, nullptr, c->d_status);
+            walk(false, grid, s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, wr, d_counts, nullptr, nullptr,
+                 nullptr, c->d_status);
         }
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
@@ -668,14 +855,40 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
             c->store_moved = true;
         }
         FillOut fo{c->dtype, 1.0 / c->w_scale, c->d_w, c->d_rowmax};
-        walk(true, nblk(nrows, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, nreps, d_counts,
-             c->d_row_ptr, c->d_idx, c->d_w64, c->d_status, fo);
+        wr.tied = use_sym ? c->d_tied : nullptr;
+        walk(true, grid, s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, wr, d_counts, c->d_row_ptr, c->d_idx,
+             c->d_w64, c->d_status, fo);
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
+        int n_retrace = 0;
+        if (use_sym) {  // mirror images of the walked rows; tied ones are walked after all
+            USPG_CUDA(c, cudaMemsetAsync(d_n_retrace, 0, sizeof(int), s));
+            k_derive<WT><<<nblk(nrows * 32, 256), 256, 0, s>>>(g, c->d_ring, nreps, d_src, d_half, d_shift,
+                                                               c->d_row_ptr, d_counts, c->d_idx, c->d_w64,
+                                                               (WT *)c->d_w, c->d_rowmax, c->d_tied, c->d_retrace,
+                                                               d_n_retrace);
+            launch_counter()++;
+            USPG_CUDA(c, cudaGetLastError());
+            USPG_CUDA(c, cudaMemcpyAsync(&n_retrace, d_n_retrace, sizeof(int), cudaMemcpyDeviceToHost, s));
+            USPG_CUDA(c, cudaStreamSynchronize(s));
+            if (n_retrace > 0) {
+                WalkRows wl;
+                wl.plan = wr.plan;
+                wl.list = c->d_retrace;
+                wl.n_list = d_n_retrace;
+                walk(true, nblk(n_retrace, TB), s, g, c->d_ring, c->d_bdir, c->d_bdirf, d_rep_view, wl, d_counts,
+                     c->d_row_ptr, c->d_idx, c->d_w64, c->d_status, fo);
+                launch_counter()++;
+                USPG_CUDA(c, cudaGetLastError());
+            }
+        }
         int st = 0;
         USPG_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         USPG_CUDA(c, cudaStreamSynchronize(s));
-        if (!(st & kStatusCountMismatch)) break;
+        if (!(st & kStatusCountMismatch)) {
+            c->gen_walked_rows = use_sym ? sp.walked_rows + n_retrace : nrows;
+            break;
+        }
         if (attempt == 1) return fail(c, USPG_EDEVICE, "generator rows changed between passes");
         USPG_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
         c->gen_fallbacks++;

@@ -183,6 +183,10 @@ struct uspg_ctx {
     size_t cap_idx = 0, cap_w = 0, cap_w64 = 0, cap_sell = 0;
     bool store_moved = false;
     int gen_fallbacks = 0;  // builds whose FP32 row bound was exceeded
+    long long gen_walked_rows = 0;  // rows the last build walked (the rest are mirror images)
+    int *d_plan = nullptr;          // transverse-symmetry tables (generator.cu)
+    int *d_tied = nullptr;          // [rows + 1] tie flag of each walked row, then a counter
+    long long *d_retrace = nullptr; // [rows] mirror rows walked after all
     long long nnz_all_views = 0;
     std::vector<long long> h_row_ptr;  // host copy for get_row
     std::vector<long long> h_rep_entry0;  // first ray-major entry of each representative (+ end)

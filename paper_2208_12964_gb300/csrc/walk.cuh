@@ -112,6 +112,7 @@ constexpr float kEps32 = 6.0e-8f;  // 2^-24, unit roundoff of FP32
 // adjacent (in ray order) to the piece they belong with.
 struct CountSink {
     int n = 0;
+    int tied = 0;  // some piece's decision lies in a tie band (classify_exact)
     uint32_t last = 0xffffffffu;
     bool outbound = false;
     uint32_t *in_cell = nullptr;
@@ -134,6 +135,7 @@ struct FillSink {
     uint32_t *idx;
     double *w;
     int n = 0;
+    int tied = 0;  // some piece's decision lies in a tie band (classify_exact)
     int cap = 0;
     uint32_t last = 0xffffffffu;
     int last_pos = -1;
@@ -171,10 +173,22 @@ struct FillSink {
     }
 };
 
+// A piece whose sector decision lies this close (in sector widths) to a
+// boundary, or whose midpoint lies this close (in ring widths) to the axis,
+// where its azimuth is ill-conditioned, makes its row "tied": the mirror
+// image of the row (transverse symmetry, generator.cu) is then traced
+// directly instead of derived, because the tie rule (counter-clockwise
+// nudge) does not commute with a reflection.  The bands are far wider than
+// the nudge and than the FP64 rounding of the two geometries.
+constexpr double kTieSector = 1e-7;
+constexpr double kTieAxis = 1e-3;
+
 // Exact classification of the piece [la, lb] (Eq. 5-10): FP64 midpoint of
 // the two crossings, ring = floor(rho / r), slab = floor((z - z_min) / h),
-// sector = floor((atan2 + nudge) n_g / 2 pi).
-USPG_HD inline uint32_t classify_exact(const Geometry &g, const RingEntry *rt, const Ray &R, double la, double lb)
+// sector = floor((atan2 + nudge) n_g / 2 pi).  *tied (optional) is set when
+// the decision lies within the tie bands above.
+USPG_HD inline uint32_t classify_exact(const Geometry &g, const RingEntry *rt, const Ray &R, double la, double lb,
+                                       int *tied = nullptr)
 {
     double pax = R.S[0] + la * R.dx, pay = R.S[1] + la * R.dy, paz = R.S[2] + la * R.dz;
     double pbx = R.S[0] + lb * R.dx, pby = R.S[1] + lb * R.dy, pbz = R.S[2] + lb * R.dz;
@@ -192,7 +206,12 @@ USPG_HD inline uint32_t classify_exact(const Geometry &g, const RingEntry *rt, c
     int ng = rt[ring].ng;
     double phi = atan2(my, mx);
     if (phi < 0.0) phi += kTwoPi;
-    long long sec = (long long)floor(((phi + kNudge) * (double)ng) / kTwoPi);
+    double xs = ((phi + kNudge) * (double)ng) / kTwoPi;
+    long long sec = (long long)floor(xs);
+    if (tied) {
+        double fr = xs - (double)sec;
+        if (fr < kTieSector || fr > 1.0 - kTieSector || rho < kTieAxis * g.r) *tied = 1;
+    }
     if (sec >= ng) sec -= ng;
     if (sec < 0) sec = 0;
     return pack_cell((int)slab, (int)ring, (int)sec);
@@ -247,7 +266,9 @@ USPG_HD inline void piece(const Geometry &g, const RingEntry *rt, const Ray &R, 
     double len = (lb - la) * R.L;
     if (lt(len, R.min_len)) return;
     uint32_t cell;
-    if (!classify_fast(g, rt, R, la, lb, &cell)) cell = classify_exact(g, rt, R, la, lb);
+    // the fast rule decides only at least ~3e-6 sector widths from a boundary
+    // and away from the axis: only exact decisions can be tied
+    if (!classify_fast(g, rt, R, la, lb, &cell)) cell = classify_exact(g, rt, R, la, lb, &sink.tied);
     sink.emit(cell, len);
 }
 

@@ -26,6 +26,9 @@ def test_rows_2d_parallel_all_views_all_rays(torch_cuda):
     o = oracle_for(spec)
     st = g.stats()
     assert st["n_reps"] == 12 and st["n_cells"] == 12480 and st["gcd"] == 6
+    # representatives at 5..25 degrees are walked, 35..55 are their mirror
+    # images; 0 and 30 degrees are their own (a parallel ray is its own mirror)
+    assert 7 * 65 <= st["walked_rows"] < 12 * 65, st["walked_rows"]
     total = 0
     for k in range(36):
         for b in range(65):
@@ -123,6 +126,11 @@ def test_rows_3d_cone_full_size_sampled(torch_cuda):
     o = oracle_for(spec)
     st = g.stats()
     assert st["n_reps"] == 15 and st["n_cells"] == 6340608
+    # transverse symmetry: representatives 1..7 are walked, 8..14 are their
+    # mirror images, representative 0 walks columns 0..127 (rows with a tied
+    # piece are walked after all)
+    base = 7 * 32768 + 128 * 128
+    assert base <= st["walked_rows"] <= base + 0.01 * 15 * 32768, st["walked_rows"]
     rng = np.random.default_rng(7)
     for _ in range(400):
         k = int(rng.integers(90))

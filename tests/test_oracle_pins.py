@@ -696,3 +696,64 @@ def test_quarter_symmetry_of_first_view_lines(case):
             assert np.allclose(ln, ln3, rtol=1e-12, atol=1e-15)
             assert all(min(int((x - y) % (1 << 64)), int((y - x) % (1 << 64))) < window
                        for x, y in zip(fa.tolist(), fa3.tolist()))
+
+
+def _mirror_rows_agree(spec, column_mirror):
+    """Rows of every representative rebuilt from its partner's under the
+    reflection y -> -y (Sec. III.C quarter symmetry): view theta -> view
+    -theta, sector j -> -1-j, then a whole number of 1/G turns up to the
+    partner's own angle; fan and cone rays swap column a <-> n_u-1-a.
+    Returns (rows compared, rows whose lists differ)."""
+    o = oracle.Oracle(spec)
+    ng, head = o.grid_tables()
+    G, V = o.G, spec["n_views"]
+    den = spec["arc_den"] * V
+    n_reps, rep_of_view, _ = o.view_classes()
+    reps = [int(np.flatnonzero(rep_of_view == q)[0]) for q in range(n_reps)]
+    key = {k: (k * spec["arc_num"] * G) % den for k in reps}
+    m = {k: (k * spec["arc_num"] * G) // den for k in reps}
+    view_of_key = {key[k]: k for k in reps}
+    n_u = spec["n_u"]
+    ring_of = np.repeat(np.arange(len(ng)), ng)
+    compared = differ = 0
+    for k in reps:
+        k2 = view_of_key.get((den - key[k]) % den)
+        if k2 is None:
+            continue
+        M = (m[k] + m[k2] + (1 if key[k] else 0)) % G
+        for ray in range(o.n_rays):
+            src = ray - ray % n_u + (n_u - 1 - ray % n_u) if column_mirror else ray
+            c, w = o.row(k, src)
+            slab, within = c // o.cells_per_slab, c % o.cells_per_slab
+            ring = ring_of[within]
+            sec = (M * (ng[ring] // G) - 1 - (within - head[ring])) % ng[ring]
+            mc = slab * o.cells_per_slab + head[ring] + sec
+            order = np.argsort(mc)
+            c2, w2 = o.row(k2, ray)
+            compared += 1
+            if not np.array_equal(mc[order], c2):
+                differ += 1
+            else:
+                assert np.allclose(w[order], w2, rtol=1e-8, atol=1e-14)  # independently rounded crossings
+    return compared, differ
+
+
+@pytest.mark.parametrize("case", ["parallel", "fan", "cone"])
+def test_partner_representatives_are_mirror_images(case):
+    """Sec. III.C: the lines of the view at -theta are the reflections of the
+    lines at theta, so representatives pair up as (rho, 1/G - rho) and only
+    one of each pair needs tracing.  Directly traced rows equal the
+    reflected, rotated rows of the partner (same lengths), on every row of
+    every pair -- a parallel scan (bins unchanged), Table 1's fan and a cone
+    (columns mirrored); the scans avoid rays through the axis."""
+    if case == "parallel":
+        spec = par2d(12, views=36, bins=26)
+        col = False
+    elif case == "fan":
+        spec = fan2d(24, 20, 40, 0.05)
+        col = True
+    else:
+        spec = cone3d(8, 6, 18, 16)
+        col = True
+    compared, differ = _mirror_rows_agree(spec, col)
+    assert compared > 0 and differ == 0, (compared, differ)
