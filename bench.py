@@ -463,6 +463,7 @@ def run_batched(args, rank, world, local):
     opts, _k = uspg.mart_opts(10, 0.2, uspg.PER_VIEW)
     b = uspg.uspg_batch_create(ctxs, opts, sp)
     info = uspg.uspg_batch_info(b)
+    tuning = uspg.uspg_batch_tuning(b)
 
     def timed(fn, k):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -498,6 +499,11 @@ def run_batched(args, rank, world, local):
                        "rings": sorted({s_["n_rings"] for s_ in specs}), "views": sorted({s_["n_views"] for s_ in specs}),
                        "iterations": 10, "graph_kernel_nodes": info["kernel_nodes"], "global_steps": info["steps"],
                        "step": "one batched run (10 per-view sweeps of every instance)"},
+            "launch_shape": {"buckets": tuning["buckets"],
+                             "probe_ms_default": round(tuning["ms_default"], 4),
+                             "probe_ms_tuned": round(tuning["ms_tuned"], 4),
+                             "gain": round(tuning["ms_default"] / tuning["ms_tuned"], 3) if tuning["ms_tuned"] else None,
+                             "how": "blocks per unit of work per ring-count bucket, tuned on the first 4 global steps"},
             "sequential": {"value": upd / (t_seq * 1e-3), "ms": t_seq,
                            "how": "the same instances, uspg_mart one after another (one graph each)"},
             "gpu_launches": int(launches), "clocks": clk.summary()}

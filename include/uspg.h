@@ -255,8 +255,9 @@ typedef struct uspg_batch uspg_batch;
  * advance together: global step t runs view step t of every context that has
  * one, as three launches covering all of them (each context gets blocks in
  * proportion to its work per view); all steps are captured in one CUDA graph.
- * Creation tunes the blocks-per-work ratio on the first steps (images are
- * saved and restored) and captures the graph.  The contexts must stay alive,
+ * Creation tunes the blocks-per-work ratios per ring-count bucket on the
+ * first steps (images are saved and restored; uspg_batch_tuning) and
+ * captures the graph.  The contexts must stay alive,
  * and must not rebuild their coefficients, until uspg_batch_destroy.
  * Synchronous.  opts->view_order, view_steps and stop_tol are ignored; the
  * batch applies the POWER rule (EUNSUPPORTED for another); errors are
@@ -267,6 +268,18 @@ uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_
 uspg_status uspg_batch_run(uspg_batch *batch, uspg_stream stream);
 /* Ray-cell updates of one run, kernel nodes in the graph, global steps. */
 uspg_status uspg_batch_info(const uspg_batch *batch, int64_t *updates_per_run, int64_t *kernel_nodes, int64_t *steps);
+/* The launch shape uspg_batch_create chose.  Instances with the same ring
+ * count form a bucket; each bucket's forward gets fwd_blocks_per_group
+ * blocks per 8-entry group of a view's rows and its correction
+ * bwd_blocks_per_slice blocks per 32-cell slice (capped at one group per
+ * thread and one slice per warp).  The shape is chosen on the first global
+ * steps: the best shape common to all buckets, then each bucket's own (kept
+ * where it gains at least 1%).  ms_default / ms_tuned: the same probe steps
+ * with the default shape and with the chosen one.  Arrays (optional) hold
+ * cap entries; *n_buckets receives the bucket count (EINVAL if above cap,
+ * with *n_buckets and the times set). */
+uspg_status uspg_batch_tuning(const uspg_batch *batch, int32_t cap, int32_t *rings, double *fwd_blocks_per_group,
+                              double *bwd_blocks_per_slice, int32_t *n_buckets, float *ms_default, float *ms_tuned);
 void uspg_batch_destroy(uspg_batch *batch);
 
 /* --- reconstruction server ------------------------------------------------------ */

@@ -115,7 +115,11 @@ struct uspg_batch {
     int max_rings = 0, max_rays = 0;
     long long nnz_per_run = 0;  // ray-cell updates of one run
     std::vector<long long> groups_view, slices_view;  // per instance: mean groups / slices per view
-    double fwd_ratio = 0, bwd_ratio = 0;               // blocks per unit of work (tuned)
+    // launch shape: blocks per unit of work (8-entry group / slice), per
+    // bucket of instances with the same ring count (tuned at creation)
+    std::vector<int> bucket_of, bucket_rings;
+    std::vector<double> fwd_ratio, bwd_ratio;
+    float ms_default = 0.0f, ms_tuned = 0.0f;  // the tuning probe's time with the default and the chosen shapes
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -127,8 +131,8 @@ static void assign_blocks(uspg_batch *b, int &mf, int &mb)
 {
     mf = mb = 1;
     for (size_t i = 0; i < b->host.size(); i++) {
-        long long fb = (long long)(b->fwd_ratio * (double)b->groups_view[i]) + 1;
-        long long bb = (long long)(b->bwd_ratio * (double)b->slices_view[i]) + 1;
+        long long fb = (long long)(b->fwd_ratio[b->bucket_of[i]] * (double)b->groups_view[i]) + 1;
+        long long bb = (long long)(b->bwd_ratio[b->bucket_of[i]] * (double)b->slices_view[i]) + 1;
         long long fmax = (b->groups_view[i] + 255) / 256 + 1, bmax = (b->slices_view[i] + 7) / 8 + 1;
         b->host[i].fwd_blocks = (int)std::min(fb, fmax);
         b->host[i].bwd_blocks = (int)std::min(bb, bmax);
@@ -290,36 +294,74 @@ uspg_status uspg_batch_create(uspg_ctx *const *ctxs, int32_t n, const uspg_mart_
             return fail(nullptr, USPG_ENOMEM, "batch: tuning scratch");
         }
     }
+    // buckets: instances with the same ring count
+    b->bucket_of.assign(n, 0);
+    for (int i = 0; i < n; i++) {
+        int rings = ctxs[i]->n_rings, q = 0;
+        while (q < (int)b->bucket_rings.size() && b->bucket_rings[q] != rings) q++;
+        if (q == (int)b->bucket_rings.size()) b->bucket_rings.push_back(rings);
+        b->bucket_of[i] = q;
+    }
+    const int nb = (int)b->bucket_rings.size();
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const double fr[4] = {1.0 / 8192, 1.0 / 2048, 1.0 / 512, 1.0 / 128};  // blocks per 8-entry group
     const double br[4] = {1.0 / 2048, 1.0 / 512, 1.0 / 128, 1.0 / 32};    // blocks per slice
     long long probe = std::min<long long>(b->max_steps, 4);
-    float best = 1e30f;
-    double bf = fr[1], bb = br[1];
+    auto time_shape = [&]() -> float {  // one warm and one timed probe
+        int mf, mb;
+        cudaStreamSynchronize(s);
+        if (upload(b, mf, mb) != cudaSuccess) return 1e30f;
+        enqueue(b, mf, mb, 0, probe, s, nullptr);
+        cudaEventRecord(e0, s);
+        enqueue(b, mf, mb, 0, probe, s, nullptr);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // the default shape, then the best shape common to all buckets
+    b->fwd_ratio.assign(nb, fr[1]);
+    b->bwd_ratio.assign(nb, br[1]);
+    b->ms_default = time_shape();
+    float best = b->ms_default;
+    double bf = fr[1], bbw = br[1];
     for (double a : fr)
         for (double c2 : br) {
-            b->fwd_ratio = a;
-            b->bwd_ratio = c2;
-            int mf, mb;
-            cudaStreamSynchronize(s);
-            if (upload(b, mf, mb) != cudaSuccess) continue;
-            enqueue(b, mf, mb, 0, probe, s, nullptr);  // warm
-            cudaEventRecord(e0, s);
-            enqueue(b, mf, mb, 0, probe, s, nullptr);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            b->fwd_ratio.assign(nb, a);
+            b->bwd_ratio.assign(nb, c2);
+            float ms = time_shape();
             if (ms < best) {
                 best = ms;
                 bf = a;
-                bb = c2;
+                bbw = c2;
             }
         }
-    b->fwd_ratio = bf;
-    b->bwd_ratio = bb;
+    b->fwd_ratio.assign(nb, bf);
+    b->bwd_ratio.assign(nb, bbw);
+    // then each bucket's own shape, the others fixed; a change must gain 1%
+    if (nb > 1) {
+        best = time_shape();
+        for (int q = 0; q < nb; q++) {
+            double qf = b->fwd_ratio[q], qb = b->bwd_ratio[q];
+            for (double a : fr)
+                for (double c2 : br) {
+                    b->fwd_ratio[q] = a;
+                    b->bwd_ratio[q] = c2;
+                    float ms = time_shape();
+                    if (ms < 0.99f * best) {
+                        best = ms;
+                        qf = a;
+                        qb = c2;
+                    }
+                }
+            b->fwd_ratio[q] = qf;
+            b->bwd_ratio[q] = qb;
+        }
+    }
+    b->ms_tuned = time_shape();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int i = 0; i < n; i++) {
@@ -359,6 +401,23 @@ uspg_status uspg_batch_run(uspg_batch *b, uspg_stream stream)
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(nullptr, USPG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
     launch_counter() += b->nodes;
+    return USPG_OK;
+}
+
+uspg_status uspg_batch_tuning(const uspg_batch *b, int32_t cap, int32_t *rings, double *fwd_blocks_per_group,
+                              double *bwd_blocks_per_slice, int32_t *n_buckets, float *ms_default, float *ms_tuned)
+{
+    if (!b || !n_buckets) return fail(nullptr, USPG_EINVAL, "NULL argument");
+    int nb = (int)b->bucket_rings.size();
+    *n_buckets = nb;
+    if (ms_default) *ms_default = b->ms_default;
+    if (ms_tuned) *ms_tuned = b->ms_tuned;
+    if (nb > cap) return fail(nullptr, USPG_EINVAL, "batch tuning: more buckets than cap");
+    for (int q = 0; q < nb; q++) {
+        if (rings) rings[q] = b->bucket_rings[q];
+        if (fwd_blocks_per_group) fwd_blocks_per_group[q] = b->fwd_ratio[q];
+        if (bwd_blocks_per_slice) bwd_blocks_per_slice[q] = b->bwd_ratio[q];
+    }
     return USPG_OK;
 }
 

@@ -112,6 +112,7 @@ def lib():
             "uspg_batch_create": ([V, I32, P(MartOpts), V, P(V)], I32),
             "uspg_batch_run": ([V, V], I32),
             "uspg_batch_info": ([V, P(I64), P(I64), P(I64)], I32),
+            "uspg_batch_tuning": ([V, I32, V, V, V, P(I32), P(C.c_float), P(C.c_float)], I32),
             "uspg_batch_destroy": ([V], None),
             "uspg_server_create": ([C.c_size_t, I32, I32, P(V)], I32),
             "uspg_server_submit": ([V, P(Job), P(C.c_uint64)], I32),
@@ -312,6 +313,21 @@ def uspg_batch_info(batch) -> dict:
     u, k, s = C.c_int64(0), C.c_int64(0), C.c_int64(0)
     _check(lib().uspg_batch_info(batch, C.byref(u), C.byref(k), C.byref(s)), None)
     return {"updates_per_run": u.value, "kernel_nodes": k.value, "steps": s.value}
+
+
+def uspg_batch_tuning(batch) -> dict:
+    cap = 64
+    rings = np.zeros(cap, np.int32)
+    fr = np.zeros(cap, np.float64)
+    br = np.zeros(cap, np.float64)
+    n = C.c_int32(0)
+    t0, t1 = C.c_float(0), C.c_float(0)
+    _check(lib().uspg_batch_tuning(batch, cap, rings.ctypes.data, fr.ctypes.data, br.ctypes.data, C.byref(n),
+                                   C.byref(t0), C.byref(t1)), None)
+    k = n.value
+    return {"buckets": [{"rings": int(rings[q]), "fwd_blocks_per_group": float(fr[q]),
+                         "bwd_blocks_per_slice": float(br[q])} for q in range(k)],
+            "ms_default": t0.value, "ms_tuned": t1.value}
 
 
 def uspg_batch_destroy(batch):

@@ -611,6 +611,9 @@ def test_batched_instances_match_oracle(torch_cuda):
     opts, _ = uspg.mart_opts(3, 0.2, uspg.PER_VIEW)
     b = uspg.uspg_batch_create([g.ctx for g in gs], opts)
     try:
+        tun = uspg.uspg_batch_tuning(b)  # one launch shape per ring count
+        assert sorted(q["rings"] for q in tun["buckets"]) == sorted({sp["n_rings"] for sp in specs})
+        assert tun["ms_default"] > 0 and tun["ms_tuned"] > 0
         uspg.uspg_batch_run(b)
         torch_cuda.cuda.synchronize()
     finally:
