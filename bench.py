@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--coeff-dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve-mixed: mean requests per second")
-    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serve-mixed: arrival window")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve-mixed: arrival window")
     ap.add_argument("--serve-sustained-seconds", type=float, default=60.0,
                     help="serve-mixed: arrival window of the run at 70%% of capacity")
     ap.add_argument("--serve-active", type=int, default=64, help="serve-mixed: jobs running at once")
