@@ -72,6 +72,12 @@ enum { USPG_LENGTH = 0, USPG_BINARY = 1 };
  *                   its source angle.  One store for all views, whatever their
  *                   angles; the ray-sequential schedule. */
 enum { USPG_STORE_REPRESENTATIVES = 0, USPG_STORE_SEGMENTS = 1 };
+/* transverse symmetry of the representative store (uspg_build_coeffs): derive
+ * the rows that are mirror images of traced rows (ALWAYS), trace every row
+ * (NEVER), or derive them when the store has more rows than the GPU traces
+ * at once (AUTO, 0; a small 2D store is traced whole in one pass, which is
+ * faster than tracing half and deriving the rest). */
+enum { USPG_SYMMETRY_AUTO = 0, USPG_SYMMETRY_ALWAYS = 1, USPG_SYMMETRY_NEVER = 2 };
 /* stored coefficient precision */
 enum { USPG_F32 = 0, USPG_F16 = 1, USPG_BF16 = 2 };
 /* MART schedules (Sec. III.D) */
@@ -127,7 +133,7 @@ typedef struct {
     int32_t weight_mode; /* USPG_LENGTH | USPG_BINARY */
     int32_t coeff_dtype; /* USPG_F32 | USPG_F16 | USPG_BF16 */
     int32_t store_form;  /* USPG_STORE_REPRESENTATIVES | USPG_STORE_SEGMENTS (binary only) */
-    int32_t reserved1;
+    int32_t symmetry;    /* USPG_SYMMETRY_AUTO | _ALWAYS | _NEVER (representative store) */
 } uspg_coeff_opts;
 
 typedef struct {

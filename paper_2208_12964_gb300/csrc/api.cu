@@ -290,6 +290,9 @@ uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, 
         return fail(nullptr, USPG_EINVAL, "unknown store_form");
     if (sf == USPG_STORE_SEGMENTS && wm != USPG_BINARY)
         return fail(nullptr, USPG_EINVAL, "the segment store holds binary coefficients (weight_mode USPG_BINARY)");
+    int sym = opts ? opts->symmetry : USPG_SYMMETRY_AUTO;
+    if (sym != USPG_SYMMETRY_AUTO && sym != USPG_SYMMETRY_ALWAYS && sym != USPG_SYMMETRY_NEVER)
+        return fail(nullptr, USPG_EINVAL, "unknown symmetry mode");
 
     uspg_ctx *c = new uspg_ctx();
     c->n_rings = g.n_rings;
@@ -312,6 +315,7 @@ uspg_status uspg_create(const uspg_grid_desc *grid, const uspg_scan_desc *scan, 
     c->mir.n_rows = c->mir.on ? (s.n_v + 1) / 2 * s.n_u : c->n_rays;
     c->weight_mode = wm;
     c->dtype = dt;
+    c->symmetry = sym;
     double unit = c->r;
     if (s.geometry == USPG_CONE_3D && c->h < unit) unit = c->h;
     c->w_scale = dt == USPG_F32 ? 1.0 : unit;

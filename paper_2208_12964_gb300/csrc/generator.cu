@@ -813,7 +813,14 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     }
     const int *d_trace = c->d_plan, *d_half = c->d_plan + nreps, *d_src = c->d_plan + 2 * nreps;
     const int *d_shift = c->d_plan + 3 * nreps, *d_all = c->d_plan + 4 * nreps, *d_zero = c->d_plan + 5 * nreps;
-    const bool sym = sp.walked_rows < nrows;
+    // the symmetry pays only when the rows are more than the GPU walks at once:
+    // a small store (a 2D scan) is walked whole in one wave, and deriving
+    // would add a second, serial walk of its tied rows
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool sym = sp.walked_rows < nrows && c->symmetry != USPG_SYMMETRY_NEVER &&
+                     (c->symmetry == USPG_SYMMETRY_ALWAYS || nrows >= 2LL * sms * 4 * TB);
     int *d_n_retrace = c->d_tied + nrows;  // counter after the flags
     // rows sized by the FP32 bound, filled by the FP64 walk; if any row
     // outgrows its bound the exact FP64 count sizes the rows instead (and

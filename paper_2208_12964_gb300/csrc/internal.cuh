@@ -140,6 +140,7 @@ struct uspg_ctx {
     uspg::Mirror mir{};  // z-mirror: stored rows per view mir.n_rows (all rays when mir.on == 0)
     // coefficient options
     int weight_mode = USPG_LENGTH, dtype = USPG_F32;
+    int symmetry = USPG_SYMMETRY_AUTO;  // transverse mirror of representative rows (uspg_coeff_opts)
     double w_scale = 1.0;  // stored weight = length / w_scale
     // view classes
     int n_reps = 0;

@@ -20,6 +20,7 @@ SECT_6N, SECT_4_2N1, SECT_CUSTOM = 0, 1, 2
 PARALLEL_2D, CONE_3D, FAN_2D = 0, 1, 2
 LENGTH, BINARY = 0, 1
 STORE_REPRESENTATIVES, STORE_SEGMENTS = 0, 1
+SYMMETRY_AUTO, SYMMETRY_ALWAYS, SYMMETRY_NEVER = 0, 1, 2
 F32, F16, BF16 = 0, 1, 2
 SEQUENTIAL, PER_VIEW = 0, 1
 POWER, LINEAR_EQ18 = 0, 1
@@ -47,7 +48,7 @@ class ScanDesc(C.Structure):
 
 class CoeffOpts(C.Structure):
     _fields_ = [("weight_mode", C.c_int32), ("coeff_dtype", C.c_int32), ("store_form", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("symmetry", C.c_int32)]
 
 
 class MartOpts(C.Structure):
@@ -174,7 +175,8 @@ def descs_from_spec(spec: dict, dtype: int = F32, weight_mode: int | None = None
         weight_mode = spec.get("weight_mode", LENGTH)
     if store_form is None:
         store_form = spec.get("store_form", STORE_REPRESENTATIVES)
-    o = CoeffOpts(weight_mode=weight_mode, coeff_dtype=dtype, store_form=store_form)
+    o = CoeffOpts(weight_mode=weight_mode, coeff_dtype=dtype, store_form=store_form,
+                  symmetry=spec.get("symmetry", SYMMETRY_AUTO))
     return g, s, o, keep
 
 

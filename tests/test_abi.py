@@ -155,3 +155,16 @@ def test_set_projections_refuses_bad_host_data(U, bad):
         assert "projection 22 (view 2, ray 4)" in msg and "finite and >= 0" in msg
     finally:
         U.uspg_destroy(ctx)
+
+
+def test_create_refuses_unknown_symmetry_mode(U):
+    from paper_2208_12964_gb300 import synth
+
+    spec = dict(synth.parallel_workload(4, 3, 9), symmetry=7)
+    g, s, o, _ = U.descs_from_spec(spec)
+    with pytest.raises(U.UspgError) as e:
+        U.uspg_create(g, s, o)
+    assert e.value.status == U.EINVAL and "symmetry" in U.uspg_last_error(None)
+    for mode in (U.SYMMETRY_AUTO, U.SYMMETRY_ALWAYS, U.SYMMETRY_NEVER):
+        g, s, o, _ = U.descs_from_spec(dict(spec, symmetry=mode))
+        U.uspg_destroy(U.uspg_create(g, s, o))

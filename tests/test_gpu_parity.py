@@ -21,7 +21,11 @@ TOL_IMG = 1e-4
 # -------------------------------------------------------------- generator ---
 
 def test_rows_2d_parallel_all_views_all_rays(torch_cuda):
+    from paper_2208_12964_gb300 import uspg
+
     spec = synth.workload("2d-parallel-64r-36v")
+    assert Gpu(spec).build().stats()["walked_rows"] == 12 * 65  # AUTO: a store this small is walked whole
+    spec["symmetry"] = uspg.SYMMETRY_ALWAYS  # every derived row below is checked
     g = Gpu(spec).build()
     o = oracle_for(spec)
     st = g.stats()
@@ -43,11 +47,14 @@ def test_rows_2d_fan_table1_all_views_all_rays(torch_cuda):
     """The paper's 2-D fan scan (Table 1): 128 rings of 4(2n-1) sectors,
     50 views over a full turn, 101 bins of 0.05, source (-8,0), detector
     (8,0); every row of every view against the oracle's direct trace."""
-    spec = synth.workload("2d-fan-128r-50v-101")
+    from paper_2208_12964_gb300 import uspg
+
+    spec = dict(synth.workload("2d-fan-128r-50v-101"), symmetry=uspg.SYMMETRY_ALWAYS)
     g = Gpu(spec).build()
     o = oracle_for(spec)
     st = g.stats()
     assert st["n_reps"] == 25 and st["n_cells"] == 65536 and st["gcd"] == 4 and not st["mirrored"]
+    assert st["walked_rows"] < 25 * 101  # mirror-image representatives derived
     total = 0
     for k in range(50):
         for a in range(101):
@@ -60,7 +67,9 @@ def test_rows_2d_fan_table1_all_views_all_rays(torch_cuda):
 
 @pytest.mark.parametrize("case", ["6n", "4_2n1", "custom"])
 def test_rows_3d_cone_small_all_rays(torch_cuda, case):
-    spec = synth.cone_workload(12, 8, 18, 24, noise=False)
+    from paper_2208_12964_gb300 import uspg
+
+    spec = dict(synth.cone_workload(12, 8, 18, 24, noise=False), symmetry=uspg.SYMMETRY_ALWAYS)
     if case == "4_2n1":
         spec["sector_rule"] = synth.SECT_4_2N1
     elif case == "custom":
@@ -84,11 +93,14 @@ def test_z_mirror_store(torch_cuda, case):
     row stored.  Every row of every view is compared with the oracle's direct
     trace, the store size with the oracle's counts, and both MART schedules
     with the oracle."""
+    from paper_2208_12964_gb300 import uspg
+
     if case == "mirror_odd":
         spec = synth.cone_workload(10, 9, 12, 21, iterations=2, lam=0.2, seed=13, noise=False)
     else:
         spec = synth.cone_workload(10, 8, 12, 20, iterations=2, lam=0.2, seed=14, noise=False)
         spec["z_min"] = -0.75  # stack [-0.75, 1.25]: not symmetric about the source plane
+    spec["symmetry"] = uspg.SYMMETRY_ALWAYS  # transverse mirror on every row checked below
     g = Gpu(spec).build()
     o = oracle_for(spec)
     n_u = n_v = spec["n_u"]
