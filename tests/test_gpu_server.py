@@ -103,17 +103,19 @@ def test_concurrent_jobs_share_one_store(torch_cuda):
     assert sum(res[j][0]["reused_store"] for j in ids) == 3
 
 
-def test_server_job_matches_the_oracle(torch_cuda):
-    """One 2D per-view job through the server against the FP64 oracle."""
+@pytest.mark.parametrize("rule", [0, 1])
+def test_server_job_matches_the_oracle(torch_cuda, rule):
+    """One 2D per-view job through the server against the FP64 oracle, with
+    the power update and with the per-view form of Eq. 18."""
     from paper_2208_12964_gb300 import uspg as U
 
     sp = synth.parallel_workload(16, 24, 33, seed=47, iterations=2, lam=0.3)
     p = synth.projections(sp)
     o = oracle_for(sp)
-    ref = o.mart_per_view(p, np.ones(o.n_cells), 2, 0.3)
+    ref = o.mart_per_view(p, np.ones(o.n_cells), 2, 0.3, rule=rule)
     srv = U.uspg_server_create(1 << 30, 2, 5)
     try:
-        opts, _ = U.mart_opts(2, 0.3, U.PER_VIEW)
+        opts, _ = U.mart_opts(2, 0.3, U.PER_VIEW, rule)
         jid = U.uspg_server_submit(srv, sp, p, opts)
         res = _wait(U, srv, [jid], {jid: o.n_cells})
     finally:
