@@ -10,6 +10,8 @@
 #include <cstring>
 #include <numeric>
 #include <sstream>
+#include <thread>
+#include <vector>
 
 namespace uspg {
 
@@ -564,20 +566,47 @@ uspg_status uspg_get_row(const uspg_ctx *cc, int32_t view, int32_t ray, int32_t 
     return USPG_OK;
 }
 
-// index of the first value that is not a finite number >= 0, or -1 (IEEE
-// bit patterns: +0 .. the largest finite float, or -0)
+// index of the first value in [b, e) that is not a finite number >= 0, or -1
+// (IEEE bit patterns: +0 .. the largest finite float, or -0)
+static long long first_bad_in(const uint32_t *u, size_t b, size_t e)
+{
+    const size_t chunk = 4096;
+    for (size_t c0 = b; c0 < e; c0 += chunk) {
+        size_t c1 = std::min(e, c0 + chunk);
+        uint32_t bad = 0;
+        for (size_t i = c0; i < c1; i++) bad |= (uint32_t)(u[i] >= 0x7f800000u) & (uint32_t)(u[i] != 0x80000000u);
+        if (bad)
+            for (size_t i = c0; i < c1; i++)
+                if (u[i] >= 0x7f800000u && u[i] != 0x80000000u) return (long long)i;
+    }
+    return -1;
+}
+
+// the same over the whole array; large arrays are split over up to 8 host
+// threads (one core reads ~20 GB/s, so a 24 MB projection set takes ~1.2 ms
+// on one core), and the smallest bad index over the parts is returned
 static long long first_bad_value(const float *p, size_t n)
 {
     const uint32_t *u = (const uint32_t *)p;
-    const size_t chunk = 4096;
-    for (size_t b = 0; b < n; b += chunk) {
-        size_t e = std::min(n, b + chunk);
-        uint32_t bad = 0;
-        for (size_t i = b; i < e; i++) bad |= (uint32_t)(u[i] >= 0x7f800000u) & (uint32_t)(u[i] != 0x80000000u);
-        if (bad)
-            for (size_t i = b; i < e; i++)
-                if (u[i] >= 0x7f800000u && u[i] != 0x80000000u) return (long long)i;
+    const size_t per_thread = (size_t)1 << 20;
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    size_t nt = std::min<size_t>({(size_t)8, (size_t)hw, (n + per_thread - 1) / per_thread});
+    if (nt <= 1) return first_bad_in(u, 0, n);
+    std::vector<long long> found(nt, -1);
+    std::vector<std::thread> pool;
+    size_t part = (n + nt - 1) / nt;
+    auto scan = [&](size_t t) { found[t] = first_bad_in(u, std::min(n, t * part), std::min(n, (t + 1) * part)); };
+    for (size_t t = 1; t < nt; t++) {
+        try {
+            pool.emplace_back(scan, t);
+        } catch (...) {  // no thread to be had: this part runs here
+            scan(t);
+        }
     }
+    scan(0);
+    for (auto &th : pool) th.join();
+    for (long long f : found)
+        if (f >= 0) return f;  // parts are in index order
     return -1;
 }
 

@@ -168,3 +168,29 @@ def test_create_refuses_unknown_symmetry_mode(U):
     for mode in (U.SYMMETRY_AUTO, U.SYMMETRY_ALWAYS, U.SYMMETRY_NEVER):
         g, s, o, _ = U.descs_from_spec(dict(spec, symmetry=mode))
         U.uspg_destroy(U.uspg_create(g, s, o))
+
+
+def test_set_projections_reports_the_first_bad_value_of_a_large_set(U):
+    """A projection set of several million values is checked in parts on
+    several host threads; the reported value is still the first bad one."""
+    import numpy as np
+
+    from paper_2208_12964_gb300 import synth
+
+    spec = synth.parallel_workload(4, 640, 4099)
+    g, s, o, _ = U.descs_from_spec(spec)
+    ctx = U.uspg_create(g, s, o)
+    try:
+        p = np.ones((640, 4099), np.float32)
+        n = p.size
+        for first in (n // 2 + 7, 5, n - 1):
+            q = p.reshape(-1).copy()
+            q[first] = np.nan
+            q[-1] = -1.0  # a later bad value in the last part
+            with pytest.raises(U.UspgError) as e:
+                U.uspg_set_projections(ctx, q.reshape(p.shape), False)
+            assert e.value.status == U.EINVAL
+            v, r = divmod(first, 4099)
+            assert f"projection {first} (view {v}, ray {r})" in U.uspg_last_error(ctx)
+    finally:
+        U.uspg_destroy(ctx)
