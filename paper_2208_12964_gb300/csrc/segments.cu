@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128) k_seg_build(Geometry g, int pass, int *co
                     phase = 1;
                     continue;
                 }
-                double l = R.t - root_k((double)m, g.r, R.d, R.a);
+                double l = R.t - root_k((double)m, g.r, R.d, R.inv_a);
                 m--;
                 if (l > R.lo && l < R.hi) return l;
             } else if (phase == 1) {
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(128) k_seg_build(Geometry g, int pass, int *co
                 if (R.d < g.r && R.t > R.lo && R.t < R.hi) return R.t;
             } else {
                 if (m > N - 1) return 2.0;
-                double l = R.t + root_k((double)m, g.r, R.d, R.a);
+                double l = R.t + root_k((double)m, g.r, R.d, R.inv_a);
                 m++;
                 if (l > R.lo && l < R.hi) return l;
             }

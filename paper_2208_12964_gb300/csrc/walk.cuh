@@ -84,6 +84,9 @@ USPG_HD inline void ray_endpoints(const Geometry &g, int k, int ray, double S[3]
 // Per-ray tracing state shared by the segment walks.
 struct Ray {
     double S[3], dx, dy, dz, L, a, t, d, lo, hi, min_len, sigma;
+    // 1 / a and 1 / dz (0 when dz = 0): the circle roots and the axial-plane
+    // parameters of the ray multiply by these instead of dividing per crossing
+    double inv_a, inv_dz;
     // FP32 copies for the fast classification: closest approach point C of
     // the XY projection (z at the same parameter) and the direction
     float cx, cy, cz, fdx, fdy, fdz;
@@ -316,7 +319,7 @@ struct ZStream {
             s += step;
             if (cs < 1 || cs > g.n_slabs - 1) continue;
             double zs = g.z_min + (double)cs * g.h;
-            next = (zs - R.S[2]) / R.dz;
+            next = (zs - R.S[2]) * R.inv_dz;
             return;
         }
     }
@@ -482,10 +485,13 @@ USPG_HD void walk_segment(const Geometry &g, const RingEntry *rt, const double2 
     if (lt(prev, sb)) piece(g, rt, R, prev, sb, sink);
 }
 
-USPG_HD inline double root_k(double m, double r, double d, double a)
+// half-chord parameter of the circle of radius m r: sqrt((m r)^2 - d^2) / |d|
+// in units of the ray parameter, with the differences taken before the
+// product (Eq. 4; the form that stays accurate near tangency)
+USPG_HD inline double root_k(double m, double r, double d, double inv_a)
 {
     double rm = m * r;
-    return sqrt(((rm - d) * (rm + d)) / a);
+    return sqrt(((rm - d) * (rm + d)) * inv_a);
 }
 
 // Full walk of one ray: set-up per Eq. 3-4, then ring segments.
@@ -506,6 +512,8 @@ USPG_HD inline bool ray_setup(const Geometry &g, int view, int ray, Ray &R, doub
     double ax = R.S[0], ay = R.S[1];
     R.a = R.dx * R.dx + R.dy * R.dy;
     if (R.a == 0.0) return false;
+    R.inv_a = 1.0 / R.a;
+    R.inv_dz = R.dz != 0.0 ? 1.0 / R.dz : 0.0;
     R.t = -(ax * R.dx + ay * R.dy) / R.a;
     double d2 = (ax * ax + ay * ay) - R.t * R.t * R.a;
     if (d2 < 0.0) d2 = 0.0;
@@ -513,7 +521,7 @@ USPG_HD inline bool ray_setup(const Geometry &g, int view, int ray, Ray &R, doub
     const int N = g.n_rings;
     double Rc = (double)N * g.r;
     if (!(R.d < Rc)) return false;
-    kR = sqrt(((Rc - R.d) * (Rc + R.d)) / R.a);
+    kR = root_k((double)N, g.r, R.d, R.inv_a);
     double lo = R.t - kR, hi = R.t + kR;
     if (lo < 0.0) lo = 0.0;
     if (hi > 1.0) hi = 1.0;
@@ -589,7 +597,7 @@ USPG_HD void walk_ray(const Geometry &g, const RingEntry *rt, const double2 *bdi
     // sink's per-ring scratch) for the outbound half
     double kout = kR;
     for (int i = N - 1; i >= m0; i--) {
-        double kin = root_k((double)i, g.r, R.d, R.a);
+        double kin = root_k((double)i, g.r, R.d, R.inv_a);
         sink.root[i] = kin;
         double a1 = R.t - kout, b1 = R.t - kin;
         walk_segment(g, rt, bdir, bdirf, R, i, a1 > lo ? a1 : lo, b1 < hi ? b1 : hi, zs, sink, status);
