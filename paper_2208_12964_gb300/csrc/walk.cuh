@@ -594,25 +594,32 @@ USPG_HD void walk_ray(const Geometry &g, const RingEntry *rt, const double2 *bdi
     zs.init(g, R, lo, hi);
     zs.advance(g, R);
     // each circle's root is formed once: the inbound half keeps it (in the
-    // sink's per-ring scratch) for the outbound half
+    // sink's per-ring scratch) for the outbound half.  One loop over the
+    // segments, so the segment walk is compiled once (a smaller kernel).
+    const int n_in = N - m0;
     double kout = kR;
-    for (int i = N - 1; i >= m0; i--) {
-        double kin = root_k((double)i, g.r, R.d, R.inv_a);
-        sink.root[i] = kin;
-        double a1 = R.t - kout, b1 = R.t - kin;
-        walk_segment(g, rt, bdir, bdirf, R, i, a1 > lo ? a1 : lo, b1 < hi ? b1 : hi, zs, sink, status);
-        kout = kin;
-    }
-    int i0 = m0 - 1;
-    double a0 = R.t - kout, b0 = R.t + kout;
-    walk_segment(g, rt, bdir, bdirf, R, i0, a0 > lo ? a0 : lo, b0 < hi ? b0 : hi, zs, sink, status);
-    sink.outbound = true;
-    double kin = kout;
-    for (int i = m0; i <= N - 1; i++) {
-        double ko = (i == N - 1) ? kR : sink.root[i + 1];
-        double a2 = R.t + kin, b2 = R.t + ko;
-        walk_segment(g, rt, bdir, bdirf, R, i, a2 > lo ? a2 : lo, b2 < hi ? b2 : hi, zs, sink, status);
-        kin = ko;
+    for (int k = 0; k <= 2 * n_in; k++) {
+        int ring;
+        double sa, sb;
+        if (k < n_in) {  // inbound: ring N-1-k
+            ring = N - 1 - k;
+            double kin = root_k((double)ring, g.r, R.d, R.inv_a);
+            sink.root[ring] = kin;
+            sa = R.t - kout;
+            sb = R.t - kin;
+            kout = kin;
+        } else if (k == n_in) {  // the deepest ring
+            ring = m0 - 1;
+            sa = R.t - kout;
+            sb = R.t + kout;
+        } else {  // outbound: ring m0 + (k - n_in - 1)
+            ring = m0 + (k - n_in - 1);
+            sink.outbound = true;
+            double ki = sink.root[ring], ko = (ring == N - 1) ? kR : sink.root[ring + 1];
+            sa = R.t + ki;
+            sb = R.t + ko;
+        }
+        walk_segment(g, rt, bdir, bdirf, R, ring, sa > lo ? sa : lo, sb < hi ? sb : hi, zs, sink, status);
     }
 }
 
