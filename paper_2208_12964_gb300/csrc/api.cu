@@ -149,8 +149,13 @@ static uspg_status ensure_state(uspg_ctx *c)
     // cell-major store: all slabs, or the lower half and the middle slab when mirrored
     int stored_slabs = c->scan.geometry == USPG_CONE_3D ? (c->mir.on ? (c->n_slabs + 1) / 2 : c->n_slabs) : 1;
     c->slices_per_rep = (long long)chunk * stored_slabs;
+    std::vector<int> slice_ring(chunk);
+    for (int i = 0; i < c->n_rings; i++)
+        for (int q = rt[i].chunk0; q < rt[i].chunk0 + (c->ng[i] + kSlice - 1) / kSlice; q++) slice_ring[q] = i;
     USPG_CUDA(c, cudaMalloc(&c->d_ring, sizeof(RingEntry) * c->n_rings));
     USPG_CUDA(c, cudaMemcpy(c->d_ring, rt.data(), sizeof(RingEntry) * c->n_rings, cudaMemcpyHostToDevice));
+    USPG_CUDA(c, cudaMalloc(&c->d_slice_ring, sizeof(int) * chunk));
+    USPG_CUDA(c, cudaMemcpy(c->d_slice_ring, slice_ring.data(), sizeof(int) * chunk, cudaMemcpyHostToDevice));
     return alloc_state(c);
 }
 
@@ -396,6 +401,7 @@ void uspg_destroy(uspg_ctx *c)
         free_store(c);
         free_segments(c);
         cudaFree(c->d_ring);
+        cudaFree(c->d_slice_ring);
         cudaFree(c->d_bdir);
         cudaFree(c->d_bdirf);
     }

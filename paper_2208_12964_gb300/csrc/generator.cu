@@ -437,7 +437,7 @@ __global__ void k_cell_count(const long long *row_ptr, const int *counts, const 
 }
 
 // one warp per slice: width = max count over its 32 cells
-__global__ void k_slice_width(const RingEntry *rt, int n_rings, int slices_per_slab, long long n_slices,
+__global__ void k_slice_width(const RingEntry *rt, const int *slice_ring, int slices_per_slab, long long n_slices,
                               long long cps, const int *cell_cnt, int *width, uint32_t *meta, int *status)
 {
     long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -445,19 +445,12 @@ __global__ void k_slice_width(const RingEntry *rt, int n_rings, int slices_per_s
     if (sl >= n_slices) return;
     int slab = (int)(sl / slices_per_slab);
     int within = (int)(sl % slices_per_slab);
-    // ring of this slice: largest ring with chunk0 <= within (binary search)
-    int lo = 0, hi = n_rings - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (rt[mid].chunk0 <= within) lo = mid;
-        else hi = mid - 1;
-    }
-    int ring = lo;
+    int ring = slice_ring[within];
     int sec0 = (within - rt[ring].chunk0) * kSlice;
     int sec = sec0 + lane;
     int c = 0;
     if (sec < rt[ring].ng) c = cell_cnt[(long long)slab * cps + rt[ring].head + sec];
-    for (int o = 16; o > 0; o >>= 1) c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+    c = __reduce_max_sync(0xffffffffu, c);
     if (lane == 0) {
         width[sl] = c;
         meta[sl] = pack_cell(slab, ring, sec0);
@@ -574,9 +567,11 @@ __global__ void k_set_off(long long *dst, const long long *rel, long long n, lon
 // cell whose column sits in arrival order at slice_off + 32 t + lane.  The
 // lane's rank (counts falling from lane 0, ties by lane) and count go to
 // lane_desc; the column, sorted by key (a total order: a ray meets a cell
-// once per view, and a key of its mirror is offset by n_rows), goes to slots 32 t + rank of the
-// lane-ordered store.  Columns of up to kOrderRegs entries are sorted in
-// registers by odd-even transposition; longer ones in place first.
+// once per view, and a key of its mirror is offset by n_rows), goes to slots
+// 32 t + rank of the lane-ordered store.  Columns of up to kOrderRegs entries
+// are sorted in registers by odd-even transposition, with the network sized
+// to the slice's longest column (slices are two or three entries wide at the
+// median); longer ones in place first.
 constexpr int kOrderRegs = 8;
 
 template <typename WT>
@@ -592,6 +587,33 @@ __device__ __forceinline__ void cx(uint32_t &ra, WT &wa, uint32_t &rb, WT &wb)
     }
 }
 
+// column of cnt <= R entries at base + 32 t: sorted in registers, written to
+// off + 32 t + rank
+template <int R, typename WT>
+__device__ __forceinline__ void order_in_regs(const uint32_t *sray, const WT *sw, long long base, int cnt,
+                                              uint32_t *dray, WT *dw, long long off, int rank)
+{
+    uint32_t r[R];
+    WT w[R];
+#pragma unroll
+    for (int t = 0; t < R; t++) {
+        r[t] = t < cnt ? sray[base + (long long)t * kSlice] : 0xffffffffu;  // absent entries sort last
+        w[t] = t < cnt ? sw[base + (long long)t * kSlice] : to_w<WT>(0.0f);
+    }
+#pragma unroll
+    for (int pass = 0; pass < R; pass++) {
+#pragma unroll
+        for (int t = pass & 1; t + 1 < R; t += 2) cx(r[t], w[t], r[t + 1], w[t + 1]);
+    }
+#pragma unroll
+    for (int t = 0; t < R; t++) {
+        if (t < cnt) {
+            dray[off + (long long)t * kSlice + rank] = r[t];
+            dw[off + (long long)t * kSlice + rank] = w[t];
+        }
+    }
+}
+
 template <typename WT>
 __global__ void k_cell_order(long long n_slices, const uint32_t *meta, const long long *slice_off,
                              const RingEntry *rt, long long cps, const int *cell_cnt, uint32_t *sray, WT *sw,
@@ -603,33 +625,30 @@ __global__ void k_cell_order(long long n_slices, const uint32_t *meta, const lon
     uint32_t m = meta[sl];
     int ring = cell_ring(m), sec = cell_sector(m) + lane;
     int cnt = sec < rt[ring].ng ? cell_cnt[(long long)cell_slab(m) * cps + rt[ring].head + sec] : 0;
-    int rank = 0;
-    for (int o = 0; o < 32; o++) {
-        int co = __shfl_sync(0xffffffffu, cnt, o);
-        rank += (co > cnt) || (co == cnt && o < lane);
+    // rank: one round per distinct count, largest first (ties by lane)
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned left = 0xffffffffu;
+    int rank = 0, above = 0, wmax = -1;
+    while (left) {
+        int c = __reduce_max_sync(0xffffffffu, (left >> lane) & 1u ? cnt : -1);
+        if (wmax < 0) wmax = c;
+        unsigned eq = __ballot_sync(0xffffffffu, ((left >> lane) & 1u) && cnt == c);
+        if ((eq >> lane) & 1u) rank = above + __popc(eq & lt_mask);
+        above += __popc(eq);
+        left &= ~eq;
     }
     lane_desc[sl * 32 + rank] = (uint16_t)((lane << 11) | cnt);
     long long off = slice_off[sl], base = off + lane;
+    if (wmax <= 2) {
+        order_in_regs<2>(sray, sw, base, cnt, dray, dw, off, rank);
+        return;
+    }
+    if (wmax <= 4) {
+        order_in_regs<4>(sray, sw, base, cnt, dray, dw, off, rank);
+        return;
+    }
     if (cnt <= kOrderRegs) {
-        uint32_t r[kOrderRegs];
-        WT w[kOrderRegs];
-#pragma unroll
-        for (int t = 0; t < kOrderRegs; t++) {
-            r[t] = t < cnt ? sray[base + (long long)t * kSlice] : 0xffffffffu;  // absent entries sort last
-            w[t] = t < cnt ? sw[base + (long long)t * kSlice] : to_w<WT>(0.0f);
-        }
-#pragma unroll
-        for (int pass = 0; pass < kOrderRegs; pass++) {
-#pragma unroll
-            for (int t = pass & 1; t + 1 < kOrderRegs; t += 2) cx(r[t], w[t], r[t + 1], w[t + 1]);
-        }
-#pragma unroll
-        for (int t = 0; t < kOrderRegs; t++) {
-            if (t < cnt) {
-                dray[off + (long long)t * kSlice + rank] = r[t];
-                dw[off + (long long)t * kSlice + rank] = w[t];
-            }
-        }
+        order_in_regs<kOrderRegs>(sray, sw, base, cnt, dray, dw, off, rank);
         return;
     }
     if (cnt <= 32) {  // insertion sort in place
@@ -942,7 +961,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         launch_counter()++;
         int *wd = c->d_slice_width + rep * n_slices;
         uint32_t *md = c->d_slice_meta + rep * n_slices;
-        k_slice_width<<<nblk(n_slices * 32, 256), 256, 0, s>>>(c->d_ring, c->n_rings, c->slices_per_slab, n_slices,
+        k_slice_width<<<nblk(n_slices * 32, 256), 256, 0, s>>>(c->d_ring, c->d_slice_ring, c->slices_per_slab, n_slices,
                                                                c->cells_per_slab, d_cell_cnt, wd, md, c->d_status);
         launch_counter()++;
         USPG_CUDA(c, exclusive_scan<int>(wd, n_slices, 1, d_rel, s));

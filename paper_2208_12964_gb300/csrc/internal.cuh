@@ -149,6 +149,7 @@ struct uspg_ctx {
     std::vector<int> m_of_view;    // rotation of each view from its representative, in 1/G turns
     // device tables
     uspg::RingEntry *d_ring = nullptr;
+    int *d_slice_ring = nullptr;  // [slices_per_slab] ring of each slice of a slab (cell-major store)
     double2 *d_bdir = nullptr;  // boundary directions, indexed head + j
     float2 *d_bdirf = nullptr;  // the same in FP32 (pre-tests)
     int slices_per_slab = 0;
