@@ -182,10 +182,7 @@ __global__ void __launch_bounds__(128) k_fill(Geometry g, const RingEntry *rt, c
     if (sink.overflow) flag(status, kStatusCountMismatch);
     counts[row] = sink.n;
     if (tied) tied[row] = sink.tied;
-    for (long long q = b + sink.n; q < e; q++) {
-        idx[q] = 0;
-        w64[q] = 0.0;
-    }
+    for (long long q = b + sink.n; q < e; q++) idx[q] = 0;  // padding (its stored weight is 0)
     int binary = g.weight_mode == USPG_BINARY;
     float mx;
     if (dtype == USPG_F16) mx = store_row(w64, b, e, sink.n, binary, inv_scale, (__half *)w);
@@ -221,8 +218,8 @@ __global__ void k_derive_caps(Geometry g, int n_reps, const int *rep_src, const 
 // for the direct walk (retrace).
 template <typename WT>
 __global__ void k_derive(Geometry g, const RingEntry *rt, int n_reps, const int *rep_src, const int *half,
-                         const int *rep_shift, const long long *row_ptr, int *counts, uint32_t *idx, double *w64,
-                         WT *w, float *rowmax, const int *tied, long long *retrace, int *n_retrace)
+                         const int *rep_shift, const long long *row_ptr, int *counts, uint32_t *idx, WT *w,
+                         float *rowmax, const int *tied, long long *retrace, int *n_retrace)
 {
     long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -244,11 +241,9 @@ __global__ void k_derive(Geometry g, const RingEntry *rt, int n_reps, const int 
             int sec = M * rt[ring].step - 1 - cell_sector(pc);
             sec = sec < 0 ? sec + ng : sec;
             idx[db + q] = pack_cell(cell_slab(pc), ring, sec);
-            w64[db + q] = w64[sb + q];
             w[db + q] = w[sb + q];
         } else {
             idx[db + q] = 0;
-            w64[db + q] = 0.0;
             w[db + q] = to_w<WT>(0.0f);
         }
     }
@@ -693,13 +688,15 @@ __global__ void k_slice_desc(uint2 *desc, const long long *slice_off, const uint
 }
 
 // ray of every aligned group of kRowPad entries of the ray-major store (rows
-// start and end on group boundaries, so a group never straddles two rays)
+// start and end on group boundaries, so a group never straddles two rays);
+// one warp per row
 __global__ void k_group_rays(const long long *row_ptr, long long n_all, int n_rows, uint32_t *grp_ray)
 {
-    long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= n_all) return;
     uint32_t ray = (uint32_t)(row % n_rows);
-    for (long long g = row_ptr[row] / kRowPad; g < row_ptr[row + 1] / kRowPad; g++) grp_ray[g] = ray;
+    long long g1 = row_ptr[row + 1] / kRowPad;
+    for (long long g = row_ptr[row] / kRowPad + (threadIdx.x & 31); g < g1; g += 32) grp_ray[g] = ray;
 }
 
 static unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -890,8 +887,8 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         if (use_sym) {  // mirror images of the walked rows; tied ones are walked after all
             USPG_CUDA(c, cudaMemsetAsync(d_n_retrace, 0, sizeof(int), s));
             k_derive<WT><<<nblk(nrows * 32, 256), 256, 0, s>>>(g, c->d_ring, nreps, d_src, d_half, d_shift,
-                                                               c->d_row_ptr, d_counts, c->d_idx, c->d_w64,
-                                                               (WT *)c->d_w, c->d_rowmax, c->d_tied, c->d_retrace,
+                                                               c->d_row_ptr, d_counts, c->d_idx, (WT *)c->d_w,
+                                                               c->d_rowmax, c->d_tied, c->d_retrace,
                                                                d_n_retrace);
             launch_counter()++;
             USPG_CUDA(c, cudaGetLastError());
@@ -1047,7 +1044,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         c->cap_grp = nnz_pad / kRowPad + 1;
         c->store_moved = true;
     }
-    k_group_rays<<<nblk(nrows, 256), 256, 0, s>>>(c->d_row_ptr, nrows, n_rows, c->d_grp_ray);
+    k_group_rays<<<nblk(nrows * 32, 256), 256, 0, s>>>(c->d_row_ptr, nrows, n_rows, c->d_grp_ray);
     launch_counter()++;
 
     USPG_CUDA(c, cudaStreamSynchronize(s));
