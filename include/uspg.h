@@ -158,6 +158,8 @@ typedef struct {
     int64_t slices;            /* cell-major slices (32 cells) per representative */
     int64_t walked_rows;       /* representative rows the FP64 walk traced; the rest are mirror images
                                   (transverse symmetry, Sec. III.C) of traced rows */
+    int64_t derived_reps;      /* representatives whose cell-major columns were derived from their
+                                  mirror source's columns (all their rows mirror images) */
 } uspg_stats;
 
 /* --- context -------------------------------------------------------------- */

@@ -476,6 +476,7 @@ uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
         o->mirrored = 0;
         o->slices = 0;
         o->walked_rows = c->n_rays;
+        o->derived_reps = 0;
         return USPG_OK;
     }
     o->n_reps = c->n_reps;
@@ -494,6 +495,7 @@ uspg_status uspg_coeff_stats(const uspg_ctx *c, uspg_stats *o)
     o->mirrored = c->mir.on;
     o->slices = c->slices_per_rep;
     o->walked_rows = c->gen_walked_rows;
+    o->derived_reps = c->gen_derived_reps;
     return USPG_OK;
 }
 

@@ -253,6 +253,47 @@ __global__ void k_derive(Geometry g, const RingEntry *rt, int n_reps, const int 
     }
 }
 
+// A row walked after all (its source row was tied) is compared with the
+// mirror image k_derive would have written, one warp per row.  Where its
+// count and cells (in order) are the mirror image's, it takes the mirror
+// image's stored weights and maximum too (they differ from its own at most
+// in FP32 rounding), so that every row of the representative is an exact
+// mirror image; where a cell differs (the tie went the other way), its
+// representative's columns cannot be derived from the source's
+// (differs[rep] = 1).
+template <typename WT>
+__global__ void k_retrace_check(Geometry g, const RingEntry *rt, const int *rep_src, const int *rep_shift,
+                                const long long *list, const int *n_list, const long long *row_ptr,
+                                const int *counts, const uint32_t *idx, WT *w, float *rowmax, int *differs)
+{
+    long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= *n_list) return;
+    long long row = list[i];
+    int rep = (int)(row / g.n_rows);
+    if (rep_src[rep] < 0) return;  // not a mirror-image representative
+    long long src = (long long)rep_src[rep] * g.n_rows + mirror_column(g, (int)(row % g.n_rows));
+    int n = counts[row];
+    long long sb = row_ptr[src], db = row_ptr[row];
+    bool diff = n != counts[src];
+    if (!diff) {
+        int M = rep_shift[rep];
+        for (int q = lane; q < n && !diff; q += 32) {
+            uint32_t pc = idx[sb + q];
+            int ring = cell_ring(pc), ng = rt[ring].ng;
+            int sec = M * rt[ring].step - 1 - cell_sector(pc);
+            sec = sec < 0 ? sec + ng : sec;
+            diff = idx[db + q] != pack_cell(cell_slab(pc), ring, sec);
+        }
+    }
+    if (__any_sync(0xffffffffu, diff)) {
+        if (lane == 0) differs[rep] = 1;
+        return;
+    }
+    for (int q = lane; q < n; q += 32) w[db + q] = w[sb + q];
+    if (lane == 0) rowmax[row] = rowmax[src];
+}
+
 // what k_fill writes besides the FP64 rows: stored weights and row maxima
 struct FillOut {
     int dtype;
@@ -582,18 +623,18 @@ __device__ __forceinline__ void cx(uint32_t &ra, WT &wa, uint32_t &rb, WT &wb)
     }
 }
 
-// column of cnt <= R entries at base + 32 t: sorted in registers, written to
-// off + 32 t + rank
-template <int R, typename WT>
-__device__ __forceinline__ void order_in_regs(const uint32_t *sray, const WT *sw, long long base, int cnt,
-                                              uint32_t *dray, WT *dw, long long off, int rank)
+// column of cnt <= R entries (load(t, key, w) fetches entry t): sorted in
+// registers, written to off + 32 t + rank
+template <int R, typename WT, class Load>
+__device__ __forceinline__ void order_in_regs(Load load, int cnt, uint32_t *dray, WT *dw, long long off, int rank)
 {
     uint32_t r[R];
     WT w[R];
 #pragma unroll
     for (int t = 0; t < R; t++) {
-        r[t] = t < cnt ? sray[base + (long long)t * kSlice] : 0xffffffffu;  // absent entries sort last
-        w[t] = t < cnt ? sw[base + (long long)t * kSlice] : to_w<WT>(0.0f);
+        r[t] = 0xffffffffu;  // absent entries sort last
+        w[t] = to_w<WT>(0.0f);
+        if (t < cnt) load(t, r[t], w[t]);
     }
 #pragma unroll
     for (int pass = 0; pass < R; pass++) {
@@ -609,44 +650,14 @@ __device__ __forceinline__ void order_in_regs(const uint32_t *sray, const WT *sw
     }
 }
 
+// a longer column, in arrival order at base + 32 t: sorted in place
+// (insertion sort, or heapsort for a cell crossed by very many rays), then
+// written to off + 32 t + rank
 template <typename WT>
-__global__ void k_cell_order(long long n_slices, const uint32_t *meta, const long long *slice_off,
-                             const RingEntry *rt, long long cps, const int *cell_cnt, uint32_t *sray, WT *sw,
-                             uint16_t *lane_desc, uint32_t *dray, WT *dw)
+__device__ void order_in_place(uint32_t *sray, WT *sw, long long base, int cnt, uint32_t *dray, WT *dw, long long off,
+                               int rank)
 {
-    long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (sl >= n_slices) return;
-    uint32_t m = meta[sl];
-    int ring = cell_ring(m), sec = cell_sector(m) + lane;
-    int cnt = sec < rt[ring].ng ? cell_cnt[(long long)cell_slab(m) * cps + rt[ring].head + sec] : 0;
-    // rank: one round per distinct count, largest first (ties by lane)
-    const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned left = 0xffffffffu;
-    int rank = 0, above = 0, wmax = -1;
-    while (left) {
-        int c = __reduce_max_sync(0xffffffffu, (left >> lane) & 1u ? cnt : -1);
-        if (wmax < 0) wmax = c;
-        unsigned eq = __ballot_sync(0xffffffffu, ((left >> lane) & 1u) && cnt == c);
-        if ((eq >> lane) & 1u) rank = above + __popc(eq & lt_mask);
-        above += __popc(eq);
-        left &= ~eq;
-    }
-    lane_desc[sl * 32 + rank] = (uint16_t)((lane << 11) | cnt);
-    long long off = slice_off[sl], base = off + lane;
-    if (wmax <= 2) {
-        order_in_regs<2>(sray, sw, base, cnt, dray, dw, off, rank);
-        return;
-    }
-    if (wmax <= 4) {
-        order_in_regs<4>(sray, sw, base, cnt, dray, dw, off, rank);
-        return;
-    }
-    if (cnt <= kOrderRegs) {
-        order_in_regs<kOrderRegs>(sray, sw, base, cnt, dray, dw, off, rank);
-        return;
-    }
-    if (cnt <= 32) {  // insertion sort in place
+    if (cnt <= 32) {
         for (int q = 1; q < cnt; q++) {
             uint32_t rv = sray[base + (long long)q * kSlice];
             WT wv = sw[base + (long long)q * kSlice];
@@ -659,7 +670,7 @@ __global__ void k_cell_order(long long n_slices, const uint32_t *meta, const lon
             sray[base + (long long)(p + 1) * kSlice] = rv;
             sw[base + (long long)(p + 1) * kSlice] = wv;
         }
-    } else {  // heapsort: a cell crossed by very many rays costs O(n log n)
+    } else {
         for (int q = cnt / 2 - 1; q >= 0; q--) sift_down(sray, sw, base, q, cnt);
         for (int e = cnt - 1; e > 0; e--) {
             long long pe = base + (long long)e * kSlice;
@@ -675,6 +686,124 @@ __global__ void k_cell_order(long long n_slices, const uint32_t *meta, const lon
     for (int t = 0; t < cnt; t++) {
         dray[off + (long long)t * kSlice + rank] = sray[base + (long long)t * kSlice];
         dw[off + (long long)t * kSlice + rank] = sw[base + (long long)t * kSlice];
+    }
+}
+
+// lane rank within a slice: counts falling from lane 0, ties by lane (one
+// round per distinct count); *wmax receives the slice's longest column
+__device__ __forceinline__ int lane_rank(int cnt, int lane, int *wmax)
+{
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned left = 0xffffffffu;
+    int rank = 0, above = 0;
+    *wmax = -1;
+    while (left) {
+        int c = __reduce_max_sync(0xffffffffu, (left >> lane) & 1u ? cnt : -1);
+        if (*wmax < 0) *wmax = c;
+        unsigned eq = __ballot_sync(0xffffffffu, ((left >> lane) & 1u) && cnt == c);
+        if ((eq >> lane) & 1u) rank = above + __popc(eq & lt_mask);
+        above += __popc(eq);
+        left &= ~eq;
+    }
+    return rank;
+}
+
+template <typename WT>
+__global__ void k_cell_order(long long n_slices, const uint32_t *meta, const long long *slice_off,
+                             const RingEntry *rt, long long cps, const int *cell_cnt, uint32_t *sray, WT *sw,
+                             uint16_t *lane_desc, uint32_t *dray, WT *dw)
+{
+    long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (sl >= n_slices) return;
+    uint32_t m = meta[sl];
+    int ring = cell_ring(m), sec = cell_sector(m) + lane;
+    int cnt = sec < rt[ring].ng ? cell_cnt[(long long)cell_slab(m) * cps + rt[ring].head + sec] : 0;
+    int wmax;
+    int rank = lane_rank(cnt, lane, &wmax);
+    lane_desc[sl * 32 + rank] = (uint16_t)((lane << 11) | cnt);
+    long long off = slice_off[sl], base = off + lane;
+    auto load = [&](int t, uint32_t &r, WT &w) {
+        r = sray[base + (long long)t * kSlice];
+        w = sw[base + (long long)t * kSlice];
+    };
+    if (wmax <= 2) order_in_regs<2>(load, cnt, dray, dw, off, rank);
+    else if (wmax <= 4) order_in_regs<4>(load, cnt, dray, dw, off, rank);
+    else if (cnt <= kOrderRegs) order_in_regs<kOrderRegs>(load, cnt, dray, dw, off, rank);
+    else order_in_place(sray, sw, base, cnt, dray, dw, off, rank);
+}
+
+// Columns of a representative whose rows are all mirror images of its
+// source's (transverse symmetry; none of its rows was walked after all):
+// cell (slab, ring, j) has the column of the source's cell (slab, ring,
+// (M step - 1 - j) mod n_g) with each ray replaced by its mirror column
+// (same n_rows offset for a mirror-ray key).  One warp per slice, read from
+// the source's finished lane-ordered store (its lane_desc gives each source
+// cell's lane rank and count) and written, sorted by the new keys, in this
+// representative's lane order -- the same store the count, scatter and
+// order passes would build from the derived rows.  Block size 256.
+template <typename WT>
+__global__ void __launch_bounds__(256) k_derive_columns(long long n_slices, int slices_per_slab, Geometry g,
+                                                        const RingEntry *rt, int shift, const uint32_t *meta,
+                                                        const long long *slice_off, const long long *src_off,
+                                                        const uint16_t *src_desc, uint32_t *sray, WT *sw,
+                                                        uint16_t *lane_desc, uint32_t *dray, WT *dw)
+{
+    __shared__ uint16_t inv[8][32];
+    long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (sl >= n_slices) return;
+    uint32_t m = meta[sl];
+    int ring = cell_ring(m), sec = cell_sector(m) + lane;
+    RingEntry e = rt[ring];
+    bool valid = sec < e.ng;
+    int ja = e.step * shift - 1 - sec;
+    if (ja < 0) ja += e.ng;
+    long long sla = (long long)cell_slab(m) * slices_per_slab + e.chunk0 + (ja >> 5);
+    int la = ja & (kSlice - 1);
+    // rank and count of each lane's source cell: one round per source slice
+    // (at most three), inverting that slice's lane order in shared memory
+    int rank_a = 0, cnt = 0;
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+        long long cur = __shfl_sync(0xffffffffu, sla, __ffs(todo) - 1);
+        uint16_t d = src_desc[cur * 32 + lane];
+        inv[wib][d >> 11] = (uint16_t)((lane << 11) | (d & 2047));
+        __syncwarp();
+        bool mine = valid && sla == cur;
+        if (mine) {
+            uint16_t v = inv[wib][la];
+            rank_a = v >> 11;
+            cnt = v & 2047;
+        }
+        __syncwarp();
+        todo &= ~__ballot_sync(0xffffffffu, mine);
+    }
+    int wmax;
+    int rank = lane_rank(cnt, lane, &wmax);
+    lane_desc[sl * 32 + rank] = (uint16_t)((lane << 11) | cnt);
+    long long off = slice_off[sl];
+    long long abase = valid ? src_off[sla] + rank_a : 0;
+    const uint32_t nr = (uint32_t)g.n_rows;
+    auto load = [&](int t, uint32_t &r, WT &w) {
+        uint32_t k = dray[abase + (long long)t * kSlice];
+        uint32_t fl = k >= nr ? nr : 0u;
+        r = (uint32_t)mirror_column(g, (int)(k - fl)) + fl;
+        w = dw[abase + (long long)t * kSlice];
+    };
+    if (wmax <= 2) order_in_regs<2>(load, cnt, dray, dw, off, rank);
+    else if (wmax <= 4) order_in_regs<4>(load, cnt, dray, dw, off, rank);
+    else if (cnt <= kOrderRegs) order_in_regs<kOrderRegs>(load, cnt, dray, dw, off, rank);
+    else {  // long column: mapped into this slice's arrival slots, then sorted in place
+        long long base = off + lane;
+        for (int t = 0; t < cnt; t++) {
+            uint32_t r;
+            WT w;
+            load(t, r, w);
+            sray[base + (long long)t * kSlice] = r;
+            sw[base + (long long)t * kSlice] = w;
+        }
+        order_in_place(sray, sw, base, cnt, dray, dw, off, rank);
     }
 }
 
@@ -843,6 +972,10 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     // every row is walked)
     long long nnz_pad = 0;
     c->gen_walked_rows = nrows;
+    // representatives whose rows are all mirror images of a source's: their
+    // columns are derived from the source's columns (k_derive_columns)
+    std::vector<char> cols_from_src(nreps, 0);
+    std::vector<int> differs;
     for (int attempt = 0; attempt < 2; attempt++) {
         const bool use_sym = attempt == 0 && sym;
         WalkRows wr;
@@ -894,6 +1027,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
             USPG_CUDA(c, cudaGetLastError());
             USPG_CUDA(c, cudaMemcpyAsync(&n_retrace, d_n_retrace, sizeof(int), cudaMemcpyDeviceToHost, s));
             USPG_CUDA(c, cudaStreamSynchronize(s));
+            for (int r = 0; r < nreps; r++) cols_from_src[r] = sp.src[r] >= 0;
             if (n_retrace > 0) {
                 WalkRows wl;
                 wl.plan = wr.plan;
@@ -903,16 +1037,29 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                      c->d_row_ptr, c->d_idx, c->d_w64, c->d_status, fo);
                 launch_counter()++;
                 USPG_CUDA(c, cudaGetLastError());
+                // representatives with a walked row that is not the mirror image build their own columns
+                int *d_differs = (int *)c->d_stats;  // scratch until the statistics below
+                USPG_CUDA(c, cudaMemsetAsync(d_differs, 0, sizeof(int) * nreps, s));
+                k_retrace_check<WT><<<nblk((long long)n_retrace * 32, 256), 256, 0, s>>>(
+                    g, c->d_ring, d_src, d_shift, c->d_retrace, d_n_retrace, c->d_row_ptr, d_counts, c->d_idx,
+                    (WT *)c->d_w, c->d_rowmax, d_differs);
+                launch_counter()++;
+                USPG_CUDA(c, cudaGetLastError());
+                differs.assign(nreps, 0);
+                USPG_CUDA(c, cudaMemcpyAsync(differs.data(), d_differs, sizeof(int) * nreps, cudaMemcpyDeviceToHost, s));
             }
         }
         int st = 0;
         USPG_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         USPG_CUDA(c, cudaStreamSynchronize(s));
+        for (int r = 0; r < nreps && r < (int)differs.size(); r++)
+            if (differs[r]) cols_from_src[r] = 0;
         if (!(st & kStatusCountMismatch)) {
             c->gen_walked_rows = use_sym ? sp.walked_rows + n_retrace : nrows;
             break;
         }
         if (attempt == 1) return fail(c, USPG_EDEVICE, "generator rows changed between passes");
+        std::fill(cols_from_src.begin(), cols_from_src.end(), 0);
         USPG_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
         c->gen_fallbacks++;
     }
@@ -1017,10 +1164,27 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     }
     // pass 2: scatter each row entry to its cell's column, then sort it into the
     // lane-ordered store
+    // (a source's columns are finished before its mirror's: sources come first)
+    c->gen_derived_reps = 0;
     for (int rep = 0; rep < nreps; rep++) {
         const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
         const int *cn = d_counts + (long long)rep * n_rows;
         const long long *so = c->d_slice_off + rep * n_slices;
+        if (cols_from_src[rep]) {
+            const int src = sp.src[rep];
+            k_slice_desc<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_desc + rep * n_slices, so,
+                                                             c->d_slice_meta + rep * n_slices, c->h_sell_base[rep],
+                                                             n_slices);
+            launch_counter()++;
+            k_derive_columns<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(
+                n_slices, c->slices_per_slab, g, c->d_ring, sp.shift[rep], c->d_slice_meta + rep * n_slices, so,
+                c->d_slice_off + src * n_slices, c->d_lane_desc + 32 * src * n_slices, c->d_sray, (WT *)c->d_sw,
+                c->d_lane_desc + 32 * rep * n_slices, c->d_cm_ray, (WT *)c->d_cm_w);
+            launch_counter()++;
+            USPG_CUDA(c, cudaGetLastError());
+            c->gen_derived_reps++;
+            continue;
+        }
         USPG_CUDA(c, cudaMemsetAsync(d_cell_fill, 0, sizeof(int) * c->n_cells, s));
         k_cell_scatter<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(
             rp, cn, c->d_idx, (const WT *)c->d_w, n_rows, M, c->d_ring, c->cells_per_slab, c->slices_per_slab, so,

@@ -186,6 +186,7 @@ struct uspg_ctx {
     bool store_moved = false;
     int gen_fallbacks = 0;  // builds whose FP32 row bound was exceeded
     long long gen_walked_rows = 0;  // rows the last build walked (the rest are mirror images)
+    int gen_derived_reps = 0;        // representatives whose columns the last build derived
     int *d_plan = nullptr;          // transverse-symmetry tables (generator.cu)
     int *d_tied = nullptr;          // [rows + 1] tie flag of each walked row, then a counter
     long long *d_retrace = nullptr; // [rows] mirror rows walked after all

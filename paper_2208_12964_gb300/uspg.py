@@ -60,7 +60,7 @@ class MartOpts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("n_cells", "cells_per_slab", "n_rays", "n_views", "n_reps", "nnz_store",
                                          "nnz_all_views", "store_bytes", "full_matrix_bytes", "max_row", "gcd",
-                                         "mirrored", "slices", "walked_rows")]
+                                         "mirrored", "slices", "walked_rows", "derived_reps")]
 
 
 class Job(C.Structure):

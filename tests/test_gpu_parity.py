@@ -130,6 +130,45 @@ def test_z_mirror_store(torch_cuda, case):
     assert rel_l2(_run_mart(g, proj, f0, 1, 0.2, 0), ref) < TOL_IMG
 
 
+@pytest.mark.parametrize("name", ["cone_mirror", "cone_16", "fan"])
+def test_derived_columns_equal_built_columns(torch_cuda, name):
+    """A representative whose rows are all mirror images of its source's
+    (transverse symmetry, Sec. III.C) gets its cell-major columns from the
+    source's finished columns, with each ray replaced by its mirror column.
+    Built with the symmetry (rows and columns derived) and without it (every
+    row walked, every column built from its rows), two per-view MART
+    iterations from the same start agree to the FP32 rounding of the ray
+    sums, and both agree with the oracle.  (A representative with a row
+    whose walk went the other way at a tie builds its own columns.)"""
+    from paper_2208_12964_gb300 import uspg
+
+    if name == "cone_mirror":
+        spec = synth.cone_workload(12, 8, 18, 24, iterations=2, lam=0.2, seed=21, noise=False)
+    elif name == "cone_16":
+        spec = synth.cone_workload(16, 16, 30, 32, iterations=2, lam=0.2, seed=22, noise=False)
+    else:  # an even bin count: no ray through the axis, whose tie rule breaks the mirror
+        spec = synth.fan_workload(64, 40, bins=100)
+    imgs, stats = {}, {}
+    proj = synth.projections(spec)
+    for mode in (uspg.SYMMETRY_ALWAYS, uspg.SYMMETRY_NEVER):
+        g = Gpu(dict(spec, symmetry=mode)).build()
+        try:
+            stats[mode] = g.stats()
+            f0 = np.ones(stats[mode]["n_cells"])
+            imgs[mode] = _run_mart(g, proj, f0, 2, 0.2, 1)
+        finally:
+            g.close()
+    assert stats[uspg.SYMMETRY_ALWAYS]["derived_reps"] > 0
+    assert stats[uspg.SYMMETRY_NEVER]["derived_reps"] == 0
+    assert stats[uspg.SYMMETRY_NEVER]["walked_rows"] > stats[uspg.SYMMETRY_ALWAYS]["walked_rows"]
+    a, b = imgs[uspg.SYMMETRY_ALWAYS], imgs[uspg.SYMMETRY_NEVER]
+    assert np.array_equal(a == 0.0, b == 0.0)
+    assert rel_l2(a, b) < 1e-6 and np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
+    o = oracle_for(spec)
+    ref = o.mart_per_view(proj, np.ones(o.n_cells), 2, 0.2)
+    assert rel_l2(a, ref) < TOL_IMG
+
+
 def test_rows_3d_cone_full_size_sampled(torch_cuda):
     """The 128-ring, 128-slab, 90-view, 256x256 workload: 400 sampled rows
     (oracle traces each one directly)."""
