@@ -472,9 +472,12 @@ __global__ void k_cell_count(const long long *row_ptr, const int *counts, const 
     }
 }
 
-// one warp per slice: width = max count over its 32 cells
+// one warp per slice: width = max count over its 32 cells.  shift >= 0: the
+// slices of a mirror-image representative, whose cell (slab, ring, j) has
+// the count of the source's cell (slab, ring, (shift step - 1 - j) mod n_g)
+// (the source's counts are in cell_cnt).
 __global__ void k_slice_width(const RingEntry *rt, const int *slice_ring, int slices_per_slab, long long n_slices,
-                              long long cps, const int *cell_cnt, int *width, uint32_t *meta, int *status)
+                              long long cps, const int *cell_cnt, int shift, int *width, uint32_t *meta, int *status)
 {
     long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -482,10 +485,18 @@ __global__ void k_slice_width(const RingEntry *rt, const int *slice_ring, int sl
     int slab = (int)(sl / slices_per_slab);
     int within = (int)(sl % slices_per_slab);
     int ring = slice_ring[within];
-    int sec0 = (within - rt[ring].chunk0) * kSlice;
+    RingEntry e = rt[ring];
+    int sec0 = (within - e.chunk0) * kSlice;
     int sec = sec0 + lane;
     int c = 0;
-    if (sec < rt[ring].ng) c = cell_cnt[(long long)slab * cps + rt[ring].head + sec];
+    if (sec < e.ng) {
+        int j = sec;
+        if (shift >= 0) {
+            j = shift * e.step - 1 - sec;
+            j = j < 0 ? j + e.ng : j;
+        }
+        c = cell_cnt[(long long)slab * cps + e.head + j];
+    }
     c = __reduce_max_sync(0xffffffffu, c);
     if (lane == 0) {
         width[sl] = c;
@@ -1095,19 +1106,31 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     // the earlier ones'; the totals are read back once)
     long long *d_rep_tot = nullptr;
     USPG_CUDA(c, cudaMallocAsync(&d_rep_tot, sizeof(long long) * (nreps + 1), s));
+    // mirror-image representative whose columns derive from rep's, or -1
+    std::vector<int> partner(nreps, -1);
+    for (int r = 0; r < nreps; r++)
+        if (cols_from_src[r]) partner[sp.src[r]] = r;
     for (int rep = 0; rep < nreps; rep++) {
         const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
         const int *cn = d_counts + (long long)rep * n_rows;
-        USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
-        k_cell_count<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(rp, cn, c->d_idx, (const WT *)c->d_w,
-                                                                           n_rows, M, c->d_ring, c->cells_per_slab,
-                                                                           d_cell_cnt);
-        launch_counter()++;
         int *wd = c->d_slice_width + rep * n_slices;
-        uint32_t *md = c->d_slice_meta + rep * n_slices;
-        k_slice_width<<<nblk(n_slices * 32, 256), 256, 0, s>>>(c->d_ring, c->d_slice_ring, c->slices_per_slab, n_slices,
-                                                               c->cells_per_slab, d_cell_cnt, wd, md, c->d_status);
-        launch_counter()++;
+        if (!cols_from_src[rep]) {  // a mirror image's widths were set with its source's counts
+            USPG_CUDA(c, cudaMemsetAsync(d_cell_cnt, 0, sizeof(int) * c->n_cells, s));
+            k_cell_count<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(
+                rp, cn, c->d_idx, (const WT *)c->d_w, n_rows, M, c->d_ring, c->cells_per_slab, d_cell_cnt);
+            launch_counter()++;
+            const int q = partner[rep];
+            k_slice_width<<<nblk(n_slices * 32, 256), 256, 0, s>>>(
+                c->d_ring, c->d_slice_ring, c->slices_per_slab, n_slices, c->cells_per_slab, d_cell_cnt, -1, wd,
+                c->d_slice_meta + rep * n_slices, c->d_status);
+            launch_counter()++;
+            if (q >= 0) {
+                k_slice_width<<<nblk(n_slices * 32, 256), 256, 0, s>>>(
+                    c->d_ring, c->d_slice_ring, c->slices_per_slab, n_slices, c->cells_per_slab, d_cell_cnt,
+                    sp.shift[q], c->d_slice_width + q * n_slices, c->d_slice_meta + q * n_slices, c->d_status);
+                launch_counter()++;
+            }
+        }
         USPG_CUDA(c, exclusive_scan<int>(wd, n_slices, 1, d_rel, s));
         k_set_off<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_off + rep * n_slices, d_rel, n_slices, d_rep_tot,
                                                       rep);
