@@ -72,11 +72,24 @@ __host__ __device__ inline int mirror_column(const Geometry &g, int ray)
 __device__ __forceinline__ bool walked(const Geometry &g, const TracePlan &P, long long gid, int *rep, int *ray)
 {
     if (gid >= (long long)P.n * g.n_rows) return false;
-    // neighbouring threads trace the same ray in different representative
-    // views: rotations about the axis, so the same rings and slabs and nearly
-    // the same sector crossings -- the walks of a warp stay in step
-    *rep = P.reps[gid % P.n];
-    *ray = (int)(gid / P.n);
+    const int nv = g.n_rows / g.n_u;  // stored detector rows
+    if (g.geometry == USPG_CONE_3D && nv > 1) {
+        // neighbouring threads trace one detector column of one
+        // representative, row after row: rays with the same projection on
+        // the transverse plane, so the same ring and sector crossings, and
+        // only their axial-plane crossings differ -- the walks of a warp stay
+        // in step
+        long long t = gid / nv;
+        int v = (int)(gid - t * nv);
+        *rep = P.reps[t % P.n];
+        int a = (int)(t / P.n);
+        *ray = v * g.n_u + a;
+    } else {
+        // the same ray in different representative views: rotations about
+        // the axis, so the same rings and nearly the same sector crossings
+        *rep = P.reps[gid % P.n];
+        *ray = (int)(gid / P.n);
+    }
     return !(P.half[*rep] && 2 * (*ray % g.n_u) > g.n_u - 1);
 }
 
