@@ -70,6 +70,10 @@ static void free_store(uspg_ctx *c)
     c->d_grp_ray = nullptr;
     c->cap_grp = 0;
     cudaFree(c->d_w64);
+    cudaFreeHost(c->h_gen_pin);
+    cudaFree(c->d_gen_small);
+    c->h_gen_pin = nullptr;
+    c->d_gen_small = nullptr;
     cudaFree(c->d_plan);
     cudaFree(c->d_tied);
     cudaFree(c->d_retrace);
@@ -174,6 +178,8 @@ uspg_status ctx_share_store(const uspg_ctx *src, uspg_ctx **out)
     c->d_counts = c->d_rep_view = c->d_cell_cnt = c->d_cell_fill = nullptr;  // generator scratch: never used
     c->d_rel = c->d_stats = nullptr;
     c->d_w64 = nullptr;
+    c->h_gen_pin = nullptr;
+    c->d_gen_small = nullptr;
     uspg_status st = alloc_state(c);
     if (st) {
         g_create_err = c->err;

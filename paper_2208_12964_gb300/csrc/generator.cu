@@ -852,6 +852,13 @@ __global__ void k_group_rays(const long long *row_ptr, long long n_all, int n_ro
     for (long long g = row_ptr[row] / kRowPad + (threadIdx.x & 31); g < g1; g += 32) grp_ray[g] = ray;
 }
 
+// first entry of each representative's rows (and the end): one read-back
+__global__ void k_rep_entry0(const long long *row_ptr, int n_reps, int n_rows, long long *out)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q <= n_reps) out[q] = row_ptr[(long long)q * n_rows];
+}
+
 static unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 Geometry make_geometry(const uspg_ctx *c)
@@ -961,8 +968,15 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_plan, sizeof(int) * 6 * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_tied, sizeof(int) * (nrows + 1)));
         USPG_CUDA(c, cudaMalloc(&c->d_retrace, sizeof(long long) * (nrows + 1)));
+        USPG_CUDA(c, cudaMallocHost(&c->h_gen_pin, sizeof(long long) * (4 * nreps + 8)));
+        USPG_CUDA(c, cudaMalloc(&c->d_gen_small, sizeof(long long) * (nreps + 1)));
         c->store_moved = true;
     }
+    // pinned read-back slots
+    long long *pin_stats = c->h_gen_pin;                   // [2 reps + 1]
+    long long *pin_entry0 = c->h_gen_pin + 2 * nreps + 1;  // [reps + 1]
+    long long *pin_tot = c->h_gen_pin + 3 * nreps + 2;     // [reps]
+    int *pin_flags = (int *)(c->h_gen_pin + 4 * nreps + 2);  // n_retrace, status, status
     int *d_rep_view = c->d_rep_view, *d_counts = c->d_counts;
 
     const int TB = 128;
@@ -1041,6 +1055,8 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         launch_counter()++;
         USPG_CUDA(c, cudaGetLastError());
         int n_retrace = 0;
+        int st = 0;
+        bool have_st = false;
         if (use_sym) {  // mirror images of the walked rows; tied ones are walked after all
             USPG_CUDA(c, cudaMemsetAsync(d_n_retrace, 0, sizeof(int), s));
             k_derive<WT><<<nblk(nrows * 32, 256), 256, 0, s>>>(g, c->d_ring, nreps, d_src, d_half, d_shift,
@@ -1049,8 +1065,12 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                                                                d_n_retrace);
             launch_counter()++;
             USPG_CUDA(c, cudaGetLastError());
-            USPG_CUDA(c, cudaMemcpyAsync(&n_retrace, d_n_retrace, sizeof(int), cudaMemcpyDeviceToHost, s));
+            USPG_CUDA(c, cudaMemcpyAsync(pin_flags, d_n_retrace, sizeof(int), cudaMemcpyDeviceToHost, s));
+            USPG_CUDA(c, cudaMemcpyAsync(pin_flags + 1, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
             USPG_CUDA(c, cudaStreamSynchronize(s));
+            n_retrace = pin_flags[0];
+            st = pin_flags[1];
+            have_st = n_retrace == 0;  // the status stands unless rows are walked again
             for (int r = 0; r < nreps; r++) cols_from_src[r] = sp.src[r] >= 0;
             if (n_retrace > 0) {
                 WalkRows wl;
@@ -1073,9 +1093,11 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                 USPG_CUDA(c, cudaMemcpyAsync(differs.data(), d_differs, sizeof(int) * nreps, cudaMemcpyDeviceToHost, s));
             }
         }
-        int st = 0;
-        USPG_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        USPG_CUDA(c, cudaStreamSynchronize(s));
+        if (!have_st) {
+            USPG_CUDA(c, cudaMemcpyAsync(pin_flags + 1, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+            USPG_CUDA(c, cudaStreamSynchronize(s));
+            st = pin_flags[1];
+        }
         for (int r = 0; r < nreps && r < (int)differs.size(); r++)
             if (differs[r]) cols_from_src[r] = 0;
         if (!(st & kStatusCountMismatch)) {
@@ -1092,23 +1114,12 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     USPG_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(long long) * (2 * nreps + 1), s));
     k_row_stats<<<nblk(nrows, 256), 256, 0, s>>>(d_counts, nrows, n_rows, M, nreps, c->d_stats);
     launch_counter()++;
-    std::vector<long long> rep_nnz(2 * nreps + 1);
-    USPG_CUDA(c, cudaMemcpyAsync(rep_nnz.data(), c->d_stats, sizeof(long long) * (2 * nreps + 1),
-                                 cudaMemcpyDeviceToHost, s));
-    USPG_CUDA(c, cudaStreamSynchronize(s));
-    long long nnz = 0, nnz_full = 0, maxrow = rep_nnz[2 * nreps];
-    for (int q = 0; q < nreps; q++) {
-        nnz_full += rep_nnz[q];
-        nnz += rep_nnz[nreps + q];
-    }
-    long long all = 0;
-    for (int k = 0; k < c->scan.n_views; k++) all += rep_nnz[c->rep_of_view[k]];
-    c->nnz_all_views = all;
+    // statistics and entry offsets: read with the slice totals below
+    USPG_CUDA(c, cudaMemcpyAsync(pin_stats, c->d_stats, sizeof(long long) * (2 * nreps + 1), cudaMemcpyDeviceToHost, s));
+    k_rep_entry0<<<nblk(nreps + 1, 128), 128, 0, s>>>(c->d_row_ptr, nreps, n_rows, c->d_gen_small);
+    launch_counter()++;
+    USPG_CUDA(c, cudaMemcpyAsync(pin_entry0, c->d_gen_small, sizeof(long long) * (nreps + 1), cudaMemcpyDeviceToHost, s));
     c->h_row_ptr.clear();  // host copy made on demand by uspg_get_row
-    c->h_rep_entry0.assign(nreps + 1, 0);
-    for (int q = 0; q <= nreps; q++)
-        USPG_CUDA(c, cudaMemcpyAsync(&c->h_rep_entry0[q], c->d_row_ptr + (long long)q * n_rows, sizeof(long long),
-                                     cudaMemcpyDeviceToHost, s));
 
     // cell-major store, one representative at a time
     if (n_slices * kSlice >= (1LL << 31))
@@ -1149,10 +1160,21 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                                                       rep);
         launch_counter()++;
     }
-    std::vector<long long> rep_tot(nreps);
-    USPG_CUDA(c, cudaMemcpyAsync(rep_tot.data(), d_rep_tot, sizeof(long long) * nreps, cudaMemcpyDeviceToHost, s));
+    USPG_CUDA(c, cudaMemcpyAsync(pin_tot, d_rep_tot, sizeof(long long) * nreps, cudaMemcpyDeviceToHost, s));
+    USPG_CUDA(c, cudaMemcpyAsync(pin_flags + 2, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     USPG_CUDA(c, cudaFreeAsync(d_rep_tot, s));
     USPG_CUDA(c, cudaStreamSynchronize(s));
+    const long long *rep_nnz = pin_stats, *rep_tot = pin_tot;
+    const int st_cm = pin_flags[2];
+    c->h_rep_entry0.assign(pin_entry0, pin_entry0 + nreps + 1);
+    long long nnz = 0, nnz_full = 0, maxrow = rep_nnz[2 * nreps];
+    for (int q = 0; q < nreps; q++) {
+        nnz_full += rep_nnz[q];
+        nnz += rep_nnz[nreps + q];
+    }
+    long long all = 0;
+    for (int k = 0; k < c->scan.n_views; k++) all += rep_nnz[c->rep_of_view[k]];
+    c->nnz_all_views = all;
     long long sell = 0;
     c->h_sell_base.assign(nreps + 1, 0);
     for (int rep = 0; rep < nreps; rep++) {
@@ -1162,13 +1184,9 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         sell += rep_tot[rep] * kSlice;
     }
     c->h_sell_base[nreps] = sell;
-    {
-        int st = 0;
-        USPG_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-        if (st & kStatusCellRays) {
-            USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
-            return fail(c, USPG_EUNSUPPORTED, "a cell is crossed by more than 2047 rays of one view");
-        }
+    if (st_cm & kStatusCellRays) {
+        USPG_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+        return fail(c, USPG_EUNSUPPORTED, "a cell is crossed by more than 2047 rays of one view");
     }
     if ((size_t)(sell + kSlice) > c->cap_sell) {
         cudaFree(c->d_sray);

@@ -194,6 +194,10 @@ struct uspg_ctx {
     std::vector<long long> h_row_ptr;  // host copy for get_row
     std::vector<long long> h_rep_entry0;  // first ray-major entry of each representative (+ end)
     std::vector<long long> h_sell_base;   // first cell-major slot of each representative
+    // pinned read-back area of the generator (statistics, entry offsets, slice
+    // totals, flags): copies into it do not stall the host until it reads them
+    long long *h_gen_pin = nullptr;
+    long long *d_gen_small = nullptr;  // [reps + 1] gathered entry offsets
     // state
     float *d_f = nullptr;
     float *d_proj = nullptr;
