@@ -601,17 +601,12 @@ __global__ void k_row_stats(const int *counts, long long n_all, int n_rows, Mirr
     if ((threadIdx.x & 31) == 0) atomicMax(&st[2 * n_reps], (unsigned long long)mx);
 }
 
-// Slice offsets of representative rep: its relative offsets (in slices of
-// 32 slots) after the slots of the earlier representatives, whose slice
-// totals are rep_tot[0 .. rep-1]; records its own total in rep_tot[rep].
-__global__ void k_set_off(long long *dst, const long long *rel, long long n, long long *rep_tot, int rep)
+// Slot offsets of all slices: 32 x the scan of all representatives' widths
+// (each representative's slices follow the earlier ones').
+__global__ void k_set_off(long long *dst, const long long *rel, long long n)
 {
-    long long base = 0;
-    for (int q = 0; q < rep; q++) base += rep_tot[q];
-    base *= kSlice;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = base + rel[i] * kSlice;
-    if (i == 0) rep_tot[rep] = rel[n];
+    if (i < n) dst[i] = rel[i] * kSlice;
 }
 
 // ---- cell-major store with lanes ordered by ray count ----------------------------
@@ -852,11 +847,12 @@ __global__ void k_group_rays(const long long *row_ptr, long long n_all, int n_ro
     for (long long g = row_ptr[row] / kRowPad + (threadIdx.x & 31); g < g1; g += 32) grp_ray[g] = ray;
 }
 
-// first entry of each representative's rows (and the end): one read-back
-__global__ void k_rep_entry0(const long long *row_ptr, int n_reps, int n_rows, long long *out)
+// every stride-th prefix sum (the first entry or slice of each
+// representative, and the end): one read-back
+__global__ void k_rep_entry0(const long long *prefix, int n_reps, int stride, long long *out)
 {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q <= n_reps) out[q] = row_ptr[(long long)q * n_rows];
+    if (q <= n_reps) out[q] = prefix[(long long)q * stride];
 }
 
 static unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -958,7 +954,7 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         USPG_CUDA(c, cudaMalloc(&c->d_rowmax, sizeof(float) * (nrows + 1)));
         USPG_CUDA(c, cudaMalloc(&c->d_cell_cnt, sizeof(int) * c->n_cells));
         USPG_CUDA(c, cudaMalloc(&c->d_cell_fill, sizeof(int) * c->n_cells));
-        USPG_CUDA(c, cudaMalloc(&c->d_rel, sizeof(long long) * (n_slices + 1)));
+        USPG_CUDA(c, cudaMalloc(&c->d_rel, sizeof(long long) * (n_slices * nreps + 1)));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_off, sizeof(long long) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_meta, sizeof(uint32_t) * n_slices * nreps));
         USPG_CUDA(c, cudaMalloc(&c->d_slice_desc, sizeof(uint2) * n_slices * nreps));
@@ -975,8 +971,8 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     // pinned read-back slots
     long long *pin_stats = c->h_gen_pin;                   // [2 reps + 1]
     long long *pin_entry0 = c->h_gen_pin + 2 * nreps + 1;  // [reps + 1]
-    long long *pin_tot = c->h_gen_pin + 3 * nreps + 2;     // [reps]
-    int *pin_flags = (int *)(c->h_gen_pin + 4 * nreps + 2);  // n_retrace, status, status
+    long long *pin_tot = c->h_gen_pin + 3 * nreps + 2;     // [reps + 1] first slice of each representative
+    int *pin_flags = (int *)(c->h_gen_pin + 4 * nreps + 3);  // n_retrace, status, status
     int *d_rep_view = c->d_rep_view, *d_counts = c->d_counts;
 
     const int TB = 128;
@@ -1126,10 +1122,8 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         return fail(c, USPG_EUNSUPPORTED, "a view's cell-major store has 2^26 slices or more");
     int *d_cell_cnt = c->d_cell_cnt, *d_cell_fill = c->d_cell_fill;
     long long *d_rel = c->d_rel;
-    // pass 1: slice widths and offsets (every representative's slots follow
-    // the earlier ones'; the totals are read back once)
-    long long *d_rep_tot = nullptr;
-    USPG_CUDA(c, cudaMallocAsync(&d_rep_tot, sizeof(long long) * (nreps + 1), s));
+    // pass 1: slice widths of every representative, then one scan over all
+    // of them: every representative's slots follow the earlier ones'
     // mirror-image representative whose columns derive from rep's, or -1
     std::vector<int> partner(nreps, -1);
     for (int r = 0; r < nreps; r++)
@@ -1155,16 +1149,19 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
                 launch_counter()++;
             }
         }
-        USPG_CUDA(c, exclusive_scan<int>(wd, n_slices, 1, d_rel, s));
-        k_set_off<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_off + rep * n_slices, d_rel, n_slices, d_rep_tot,
-                                                      rep);
-        launch_counter()++;
     }
-    USPG_CUDA(c, cudaMemcpyAsync(pin_tot, d_rep_tot, sizeof(long long) * nreps, cudaMemcpyDeviceToHost, s));
+    const long long all_slices = (long long)nreps * n_slices;
+    USPG_CUDA(c, exclusive_scan<int>(c->d_slice_width, all_slices, 1, d_rel, s));
+    k_set_off<<<nblk(all_slices, 256), 256, 0, s>>>(c->d_slice_off, d_rel, all_slices);
+    launch_counter()++;
+    k_rep_entry0<<<nblk(nreps + 1, 128), 128, 0, s>>>(d_rel, nreps, (int)n_slices, c->d_gen_small);
+    launch_counter()++;
+    USPG_CUDA(c, cudaMemcpyAsync(pin_tot, c->d_gen_small, sizeof(long long) * (nreps + 1), cudaMemcpyDeviceToHost, s));
     USPG_CUDA(c, cudaMemcpyAsync(pin_flags + 2, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    USPG_CUDA(c, cudaFreeAsync(d_rep_tot, s));
     USPG_CUDA(c, cudaStreamSynchronize(s));
-    const long long *rep_nnz = pin_stats, *rep_tot = pin_tot;
+    std::vector<long long> rep_tot(nreps);  // slices of each representative
+    for (int r = 0; r < nreps; r++) rep_tot[r] = pin_tot[r + 1] - pin_tot[r];
+    const long long *rep_nnz = pin_stats;
     const int st_cm = pin_flags[2];
     c->h_rep_entry0.assign(pin_entry0, pin_entry0 + nreps + 1);
     long long nnz = 0, nnz_full = 0, maxrow = rep_nnz[2 * nreps];
