@@ -828,11 +828,13 @@ __global__ void __launch_bounds__(256) k_derive_columns(long long n_slices, int 
 
 // Correction descriptors of one representative's slices: {first slot
 // relative to the representative's base, meta}, one 8-byte load per slice.
-__global__ void k_slice_desc(uint2 *desc, const long long *slice_off, const uint32_t *meta, long long base,
-                             long long n)
+// All representatives in one launch: rep_first[r] is representative r's
+// first slice in the scan of all widths (its slots start at 32 x that).
+__global__ void k_slice_desc(uint2 *desc, const long long *slice_off, const uint32_t *meta,
+                             const long long *rep_first, long long n_slices, long long n)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) desc[i] = make_uint2((uint32_t)(slice_off[i] - base), meta[i]);
+    if (i < n) desc[i] = make_uint2((uint32_t)(slice_off[i] - rep_first[i / n_slices] * kSlice), meta[i]);
 }
 
 // ray of every aligned group of kRowPad entries of the ray-major store (rows
@@ -1216,6 +1218,9 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
     // pass 2: scatter each row entry to its cell's column, then sort it into the
     // lane-ordered store
     // (a source's columns are finished before its mirror's: sources come first)
+    k_slice_desc<<<nblk(all_slices, 256), 256, 0, s>>>(c->d_slice_desc, c->d_slice_off, c->d_slice_meta,
+                                                        c->d_gen_small, n_slices, all_slices);
+    launch_counter()++;
     c->gen_derived_reps = 0;
     for (int rep = 0; rep < nreps; rep++) {
         const long long *rp = c->d_row_ptr + (long long)rep * n_rows;
@@ -1223,10 +1228,6 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         const long long *so = c->d_slice_off + rep * n_slices;
         if (cols_from_src[rep]) {
             const int src = sp.src[rep];
-            k_slice_desc<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_desc + rep * n_slices, so,
-                                                             c->d_slice_meta + rep * n_slices, c->h_sell_base[rep],
-                                                             n_slices);
-            launch_counter()++;
             k_derive_columns<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(
                 n_slices, c->slices_per_slab, g, c->d_ring, sp.shift[rep], c->d_slice_meta + rep * n_slices, so,
                 c->d_slice_off + src * n_slices, c->d_lane_desc + 32 * src * n_slices, c->d_sray, (WT *)c->d_sw,
@@ -1240,10 +1241,6 @@ static uspg_status build_typed(uspg_ctx *c, cudaStream_t s)
         k_cell_scatter<WT><<<nblk((long long)n_rows * 32, 256), 256, 0, s>>>(
             rp, cn, c->d_idx, (const WT *)c->d_w, n_rows, M, c->d_ring, c->cells_per_slab, c->slices_per_slab, so,
             d_cell_fill, c->d_sray, (WT *)c->d_sw);
-        launch_counter()++;
-        k_slice_desc<<<nblk(n_slices, 256), 256, 0, s>>>(c->d_slice_desc + rep * n_slices, so,
-                                                         c->d_slice_meta + rep * n_slices, c->h_sell_base[rep],
-                                                         n_slices);
         launch_counter()++;
         // the scatter's slot counters now hold every cell's count
         k_cell_order<WT><<<nblk(n_slices * 32, 256), 256, 0, s>>>(
