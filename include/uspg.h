@@ -211,13 +211,16 @@ uspg_status uspg_get_row(const uspg_ctx *ctx, int32_t view, int32_t ray, int32_t
 /* --- data in / out ------------------------------------------------------------ */
 
 /* Projections P_{p,l} of Eq. 17, float32 [views][rays], copied into the
- * context (host source: staged with cudaMemcpyAsync, so the call may return
- * before the copy ends only for page-locked memory).  Every value must be a
- * finite number >= 0 (measured line integrals; noisy data clamped at 0).  Host
- * data are checked before anything is copied: EINVAL names the first bad
- * value.  Device data are checked while they are copied: a bad value raises
- * the context's device flag, which the next uspg_sync reports as EDEVICE.  A
- * ray whose value is bad is skipped by every schedule (it changes no cell). */
+ * context.  Every value must be a finite number >= 0 (measured line
+ * integrals; noisy data clamped at 0).  Host data are checked before the
+ * context's projections change: EINVAL names the first bad value and leaves
+ * them as they were.  A set of fewer than 2^20 values is checked on the host
+ * and copied with cudaMemcpyAsync (the call may return before the copy ends
+ * only for page-locked memory); a larger one is copied to a device staging
+ * buffer, checked there (the call waits for the check) and then copied on.
+ * Device data are checked while they are copied: a bad value raises the
+ * context's device flag, which the next uspg_sync reports as EDEVICE.  A ray
+ * whose value is bad is skipped by every schedule (it changes no cell). */
 uspg_status uspg_set_projections(uspg_ctx *ctx, const float *p, int32_t on_device, uspg_stream stream);
 /* Image f_v, float32 [cells]. */
 uspg_status uspg_set_image(uspg_ctx *ctx, const float *f, int32_t on_device, uspg_stream stream);

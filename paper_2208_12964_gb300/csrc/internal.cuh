@@ -201,6 +201,8 @@ struct uspg_ctx {
     // state
     float *d_f = nullptr;
     float *d_proj = nullptr;
+    float *d_proj_stage = nullptr;         // large host projections land here to be checked (set_projections)
+    unsigned long long *d_first_bad = nullptr;
     bool have_proj = false;
     float *d_res = nullptr;  // per-ray correction terms (float2 [n_rays], or float4 [2 n_rows] mirrored)
     int *d_status = nullptr;

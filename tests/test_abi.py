@@ -170,9 +170,12 @@ def test_create_refuses_unknown_symmetry_mode(U):
         U.uspg_destroy(U.uspg_create(g, s, o))
 
 
-def test_set_projections_reports_the_first_bad_value_of_a_large_set(U):
-    """A projection set of several million values is checked in parts on
-    several host threads; the reported value is still the first bad one."""
+@pytest.mark.gpu
+def test_set_projections_reports_the_first_bad_value_of_a_large_set(U, torch_cuda):
+    """A projection set of a million values or more is copied to a staging
+    buffer and checked on the device before the context's projections
+    change; the reported value is the first bad one, and a refused set
+    leaves the projections as they were."""
     import numpy as np
 
     from paper_2208_12964_gb300 import synth
@@ -192,5 +195,7 @@ def test_set_projections_reports_the_first_bad_value_of_a_large_set(U):
             assert e.value.status == U.EINVAL
             v, r = divmod(first, 4099)
             assert f"projection {first} (view {v}, ray {r})" in U.uspg_last_error(ctx)
+        U.uspg_set_projections(ctx, p, False)  # a good set goes through
+        U.uspg_sync(ctx)
     finally:
         U.uspg_destroy(ctx)
