@@ -130,8 +130,13 @@ static void free_state(uspg_ctx *c)
     cudaFree(c->d_proj);
     cudaFree(c->d_proj_stage);
     cudaFree(c->d_first_bad);
+    cudaFree(c->d_rs_std);
+    cudaFree(c->d_rs_out);
     c->d_proj_stage = nullptr;
     c->d_first_bad = nullptr;
+    c->d_rs_std = nullptr;
+    c->d_rs_out = nullptr;
+    c->cap_rs_out = 0;
     cudaFree(c->d_res);
     cudaFree(c->d_sacc);
     cudaFree(c->d_status);
@@ -178,6 +183,9 @@ uspg_status ctx_share_store(const uspg_ctx *src, uspg_ctx **out)
     c->d_f = c->d_proj = c->d_res = c->d_sacc = nullptr;
     c->d_proj_stage = nullptr;
     c->d_first_bad = nullptr;
+    c->d_rs_std = nullptr;
+    c->d_rs_out = nullptr;
+    c->cap_rs_out = 0;
     c->d_status = c->d_sweeps = nullptr;
     c->cap_stream = nullptr;
     c->d_counts = c->d_rep_view = c->d_cell_cnt = c->d_cell_fill = nullptr;  // generator scratch: never used
@@ -994,12 +1002,20 @@ uspg_status uspg_resample_cartesian(uspg_ctx *c, int32_t mode, int32_t nx, int32
     cudaStream_t s = (cudaStream_t)stream;
     size_t bytes = sizeof(float) * (size_t)nx * ny * ns;
     float *dst = out;
-    if (!out_on_device) USPG_CUDA(c, cudaMallocAsync(&dst, bytes, s));
+    if (!out_on_device) {  // the context's device image for host destinations, kept between calls
+        if (bytes > c->cap_rs_out) {
+            USPG_CUDA(c, cudaStreamSynchronize(s));
+            cudaFree(c->d_rs_out);
+            c->d_rs_out = nullptr;
+            USPG_CUDA(c, cudaMalloc(&c->d_rs_out, bytes));
+            c->cap_rs_out = bytes;
+        }
+        dst = c->d_rs_out;
+    }
     st = launch_resample(c, mode, nx, ny, dst, s);
     if (st) return st;
     if (!out_on_device) {
         USPG_CUDA(c, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s));
-        USPG_CUDA(c, cudaFreeAsync(dst, s));
         USPG_CUDA(c, cudaStreamSynchronize(s));
     }
     return USPG_OK;

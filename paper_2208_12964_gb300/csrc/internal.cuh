@@ -202,6 +202,9 @@ struct uspg_ctx {
     float *d_f = nullptr;
     float *d_proj = nullptr;
     float *d_proj_stage = nullptr;         // large host projections land here to be checked (set_projections)
+    float *d_rs_std = nullptr;             // resample: the image in the standard layout (mirrored contexts)
+    float *d_rs_out = nullptr;             // resample: device image for a host destination
+    size_t cap_rs_out = 0;
     unsigned long long *d_first_bad = nullptr;
     bool have_proj = false;
     float *d_res = nullptr;  // per-ray correction terms (float2 [n_rays], or float4 [2 n_rows] mirrored)

@@ -80,11 +80,10 @@ uspg_status launch_resample(uspg_ctx *c, int mode, int nx, int ny, float *out, c
     int ns = c->scan.geometry == USPG_CONE_3D ? c->n_slabs : 1;
     const int TB = 256;
     const float *f = c->d_f;
-    float *tmp = nullptr;
-    if (c->mir.on) {  // mirrored image pairs -> standard layout
-        USPG_CUDA(c, cudaMallocAsync(&tmp, sizeof(float) * c->n_cells, s));
-        USPG_CUDA(c, image_from_pairs(c, c->d_f, tmp, s));
-        f = tmp;
+    if (c->mir.on) {  // mirrored image pairs -> standard layout (a buffer the context keeps)
+        if (!c->d_rs_std) USPG_CUDA(c, cudaMalloc(&c->d_rs_std, sizeof(float) * c->n_cells));
+        USPG_CUDA(c, image_from_pairs(c, c->d_f, c->d_rs_std, s));
+        f = c->d_rs_std;
     }
     if (mode == USPG_RESAMPLE_POINT) {
         long long n = (long long)nx * ny;
@@ -97,7 +96,6 @@ uspg_status launch_resample(uspg_ctx *c, int mode, int nx, int ny, float *out, c
     }
     launch_counter()++;
     USPG_CUDA(c, cudaGetLastError());
-    if (tmp) USPG_CUDA(c, cudaFreeAsync(tmp, s));
     return USPG_OK;
 }
 
